@@ -1,0 +1,127 @@
+"""Seeded synthetic circuits: the workloads the simulator is measured on.
+
+This module generates inputs only. It holds none of the simulator's arithmetic (no
+quantization, coding, normalization or gate application): it emits lists of gates
+(FP64 matrices computed on the host, target and control qubits) that the CUDA path and
+the CPU oracle consume identically.
+
+Workload shapes follow the paper's evaluation (Sec. III): the Quantum Fourier Transform
+and Grover's search, plus random brickwork circuits as a poorly compressible stress case.
+Qubit q is bit q of the amplitude index (little-endian). A gate's targets[0] is the least
+significant bit of its matrix's basis index.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+from typing import List, Sequence, Tuple
+
+import numpy as np
+
+
+@dataclass(frozen=True)
+class Gate:
+    matrix: np.ndarray            # complex128, shape (2^k, 2^k)
+    targets: Tuple[int, ...]
+    controls: Tuple[int, ...] = ()
+    name: str = ""
+
+    @property
+    def k(self) -> int:
+        return len(self.targets)
+
+
+S2 = 1.0 / math.sqrt(2.0)
+H = np.array([[S2, S2], [S2, -S2]], dtype=np.complex128)
+X = np.array([[0, 1], [1, 0]], dtype=np.complex128)
+Z = np.array([[1, 0], [0, -1]], dtype=np.complex128)
+SWAP = np.array([[1, 0, 0, 0], [0, 0, 1, 0], [0, 1, 0, 0], [0, 0, 0, 1]], dtype=np.complex128)
+
+
+def phase(m: int) -> np.ndarray:
+    """R_m = diag(1, exp(2 pi i / 2^m))."""
+    a = 2.0 * math.pi / float(1 << m)
+    return np.array([[1, 0], [0, complex(math.cos(a), math.sin(a))]], dtype=np.complex128)
+
+
+def splitmix64(x: int) -> int:
+    """SplitMix64 output for state x (published constants of the SplitMix64 generator)."""
+    x = (x + 0x9E3779B97F4A7C15) & 0xFFFFFFFFFFFFFFFF
+    z = x
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & 0xFFFFFFFFFFFFFFFF
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & 0xFFFFFFFFFFFFFFFF
+    return z ^ (z >> 31)
+
+
+def seeded_index(seed: int, n: int) -> int:
+    """A seeded uniformly random n-bit basis index."""
+    return splitmix64(seed) & ((1 << n) - 1)
+
+
+def qft(n: int) -> List[Gate]:
+    """QFT on n qubits: H, then controlled R_m from every less significant qubit, for each
+    qubit from the most significant down; then the bit-reversal SWAPs.
+    On |x> it produces 2^{-n/2} sum_y exp(2 pi i x y / 2^n) |y>.
+    Gate count: n + n(n-1)/2 + floor(n/2)."""
+    gates: List[Gate] = []
+    for j in range(n - 1, -1, -1):
+        gates.append(Gate(H, (j,), (), "H"))
+        for k in range(j - 1, -1, -1):
+            gates.append(Gate(phase(j - k + 1), (j,), (k,), "CR%d" % (j - k + 1)))
+    for i in range(n // 2):
+        gates.append(Gate(SWAP, (i, n - 1 - i), (), "SWAP"))
+    return gates
+
+
+def grover_iterations(n: int) -> int:
+    return int(math.floor(math.pi / 4.0 * math.sqrt(float(1 << n))))
+
+
+def _mcz(n: int) -> Gate:
+    """Z on qubit 0 controlled by qubits 1..n-1: a phase flip of |1...1>."""
+    return Gate(Z, (0,), tuple(range(1, n)), "MCZ")
+
+
+def grover(n: int, marked: int, iterations: int | None = None) -> List[Gate]:
+    """Grover search: H on every qubit, then `iterations` rounds of
+    oracle (X on the zero bits of `marked`, MCZ, X) and diffusion (H^n X^n MCZ X^n H^n)."""
+    if iterations is None:
+        iterations = grover_iterations(n)
+    zeros = [q for q in range(n) if not (marked >> q) & 1]
+    gates: List[Gate] = [Gate(H, (q,), (), "H") for q in range(n)]
+    for _ in range(iterations):
+        gates += [Gate(X, (q,), (), "X") for q in zeros]
+        gates.append(_mcz(n))
+        gates += [Gate(X, (q,), (), "X") for q in zeros]
+        gates += [Gate(H, (q,), (), "H") for q in range(n)]
+        gates += [Gate(X, (q,), (), "X") for q in range(n)]
+        gates.append(_mcz(n))
+        gates += [Gate(X, (q,), (), "X") for q in range(n)]
+        gates += [Gate(H, (q,), (), "H") for q in range(n)]
+    return gates
+
+
+def haar_su2(rng: np.random.Generator) -> np.ndarray:
+    """Haar-random SU(2) from a normalized 4-Gaussian quaternion (a, b, c, d):
+    [[a + ib, c + id], [-c + id, a - ib]]."""
+    v = rng.standard_normal(4)
+    a, b, c, d = v / np.linalg.norm(v)
+    return np.array([[complex(a, b), complex(c, d)], [complex(-c, d), complex(a, -b)]], dtype=np.complex128)
+
+
+def random_brickwork(n: int, depth: int, seed: int) -> List[Gate]:
+    """Each layer: a Haar SU(2) on every qubit, then CZ on nearest-neighbour pairs starting
+    at qubit 0 on even layers and at qubit 1 on odd layers."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    gates: List[Gate] = []
+    for layer in range(depth):
+        for q in range(n):
+            gates.append(Gate(haar_su2(rng), (q,), (), "U"))
+        for q in range(layer % 2, n - 1, 2):
+            gates.append(Gate(Z, (q + 1,), (q,), "CZ"))
+    return gates
+
+
+def count_amplitude_updates(n: int, gates: Sequence[Gate]) -> int:
+    """Amplitude-updates of a circuit: 2^n per (unfused) gate."""
+    return (1 << n) * len(gates)

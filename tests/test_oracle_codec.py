@@ -1,0 +1,249 @@
+"""Pins for the oracle's block codec (Sec. II: SZ-style error-bounded lossy compression,
+restated as absolute-bound linear quantization, a 1-D Lorenzo predictor on the integer
+codes, 16-bit symbols and canonical Huffman coding).
+
+What pins it: the pointwise error bound |x - x'| <= eb evaluated in FP64, losslessness of
+the entropy-coding layers (round trip, idempotence), an independent heap-based textbook
+Huffman (optimal total cost is unique), the Kraft equality, the Fibonacci depth bound and
+a structural parse of the documented byte layout."""
+import heapq
+import math
+import struct
+
+import numpy as np
+import pytest
+
+import oracle
+
+B_LOG2 = [5, 8, 12]
+
+
+def gen_block(kind, b, rng, dtype):
+    B = 1 << b
+    if kind == "normal":
+        v = (rng.standard_normal(B) + 1j * rng.standard_normal(B)) * 1e-3
+    elif kind == "qft":  # unit-modulus phases scaled like a 2^-n/2 amplitude
+        ph = rng.uniform(0, 2 * np.pi) + np.arange(B) * rng.uniform(0, 2 * np.pi)
+        v = np.exp(1j * ph) * 2.0 ** -8
+    elif kind == "grover":  # one value almost everywhere, a spike
+        v = np.full(B, 2.0 ** -10 + 0j)
+        v[rng.integers(B)] = 0.7
+    elif kind == "walsh":  # +-c sign patterns: large Lorenzo deltas (escapes)
+        v = 0.01 * (1 - 2 * (np.arange(B) & 1)) + 0j
+    elif kind == "zeros":
+        v = np.zeros(B, dtype=np.complex128)
+    elif kind == "const":
+        v = np.full(B, 0.125 - 0.25j)
+    elif kind == "wide":  # many distinct symbols: forces PACK
+        v = (rng.standard_normal(B) + 1j * rng.standard_normal(B)) * 0.05
+    else:
+        raise ValueError(kind)
+    return v.astype(np.complex64 if dtype == oracle.C64 else np.complex128)
+
+
+KINDS = ["normal", "qft", "grover", "walsh", "zeros", "const", "wide"]
+
+
+def reconstruct(x, eb, dtype):
+    """Elementwise reconstruction the codec must reproduce after its lossless layers:
+    x' = fl(rint(fl(x r)) * 2eb) (complex64: rounded to float), or x itself (verbatim)."""
+    xd = np.asarray(x, dtype=np.float64)
+    two = 2.0 * eb
+    r = 1.0 / two
+    t = xd * r
+    ok = np.abs(t) < 2.0 ** 29
+    q = np.where(ok, np.rint(np.where(ok, t, 0.0)), 0.0)
+    xr = q * two
+    if dtype == oracle.C64:
+        xr = xr.astype(np.float32).astype(np.float64)
+    with np.errstate(invalid="ignore"):
+        ok &= np.abs(xd - xr) <= eb
+    return np.where(ok, xr, xd), ~ok
+
+
+def as_real(v):
+    return np.stack([v.real, v.imag], axis=-1).reshape(-1)
+
+
+@pytest.mark.parametrize("dtype", [oracle.C128, oracle.C64])
+@pytest.mark.parametrize("b", B_LOG2)
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("eb", [1e-4, 1e-6, 1e-8])
+def test_pointwise_bound_and_roundtrip(dtype, b, kind, eb):
+    rng = np.random.default_rng(hash((dtype, b, kind)) % 2**32)
+    v = gen_block(kind, b, rng, dtype)
+    stream, info = oracle.compress_block(v, b, dtype, eb)
+    d = oracle.decompress_block(stream, b, dtype, eb)
+    x = as_real(v).astype(np.float64)
+    xd = as_real(d).astype(np.float64)
+    # pointwise error bound, evaluated in FP64
+    assert np.all(np.abs(x - xd) <= eb)
+    # the entropy-coding layers are lossless
+    ref, verb = reconstruct(as_real(v), eb, dtype)
+    assert np.array_equal(xd, ref)
+    assert info["n_verbatim"] == int(verb.sum())
+    assert len(stream) % 16 == 0
+    # compressing the reconstruction again gives the same stream (idempotence), where
+    # the float grid is fine enough for the quantization grid (always for complex128)
+    if dtype == oracle.C128 or np.abs(x).max() * 2.0 ** -23 < eb:
+        stream2, _ = oracle.compress_block(d, b, dtype, eb)
+        assert stream2 == stream
+
+
+def test_zero_block_is_const_header_only():
+    for dtype in (oracle.C64, oracle.C128):
+        for b in B_LOG2:
+            z = np.zeros(1 << b, dtype=np.complex128)
+            s, info = oracle.compress_block(z, b, dtype, 1e-6)
+            assert info["mode"] == oracle.MODE_CONST and len(s) == 16
+            assert np.array_equal(oracle.decompress_block(s, b, dtype, 1e-6), z)
+
+
+def test_modes_selected_by_rule():
+    rng = np.random.default_rng(0)
+    s, info = oracle.compress_block(gen_block("const", 8, rng, oracle.C128), 8, oracle.C128, 1e-6)
+    assert info["mode"] == oracle.MODE_CONST
+    # peaked (Gaussian) deltas: Huffman beats fixed width
+    v = gen_block("normal", 12, rng, oracle.C128)
+    s, info = oracle.compress_block(v, 12, oracle.C128, 1e-5)
+    assert info["mode"] == oracle.MODE_HUFF and info["n_distinct"] <= 1024
+    s, info = oracle.compress_block(gen_block("wide", 12, rng, oracle.C128), 12, oracle.C128, 1e-6)
+    assert info["n_distinct"] > 1024 and info["mode"] == oracle.MODE_PACK
+
+
+def test_escapes_roundtrip():
+    rng = np.random.default_rng(1)
+    v = gen_block("walsh", 8, rng, oracle.C128)
+    s, info = oracle.compress_block(v, 8, oracle.C128, 1e-8)
+    assert info["n_escape"] > 0
+    d = oracle.decompress_block(s, 8, oracle.C128, 1e-8)
+    assert np.all(np.abs(as_real(d) - as_real(v)) <= 1e-8)
+
+
+def test_verbatim_values_exact():
+    b = 6
+    v = np.zeros(1 << b, dtype=np.complex128)
+    v[3] = 1e6 + 0j            # |x r| >= 2^29: out of the quantizer's range
+    v[7] = complex(np.inf, 1.0)
+    v[9] = complex(0.5, np.nan)
+    s, info = oracle.compress_block(v, b, oracle.C128, 1e-6)
+    assert info["n_verbatim"] == 3
+    d = oracle.decompress_block(s, b, oracle.C128, 1e-6)
+    assert as_real(d).tobytes() == as_real(v).tobytes()
+
+
+def textbook_huffman_cost(freqs):
+    """Classic heap construction; its total cost sum(f * depth) is the optimum."""
+    if len(freqs) == 1:
+        return freqs[0]
+    h = list(freqs)
+    heapq.heapify(h)
+    cost = 0
+    while len(h) > 1:
+        a = heapq.heappop(h)
+        b = heapq.heappop(h)
+        cost += a + b
+        heapq.heappush(h, a + b)
+    return cost
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_huffman_optimal_and_complete(seed):
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(2, 600))
+    f = rng.integers(1, [2, 10, 1000, 100000][seed % 4], size=n).astype(np.uint32)
+    syms = rng.choice(65536, size=n, replace=False).astype(np.uint32)
+    L = oracle.huffman_lengths(f, syms)
+    assert int((f.astype(np.int64) * L).sum()) == textbook_huffman_cost([int(x) for x in f])
+    # a full binary tree: Kraft sum exactly 1
+    assert sum(2.0 ** -int(l) for l in L) == 1.0
+
+
+def test_huffman_fibonacci_depth_bound():
+    fib = [1, 1]
+    while len(fib) < 19:
+        fib.append(fib[-1] + fib[-2])
+    L = oracle.huffman_lengths(np.array(fib, dtype=np.uint32))
+    assert L.max() == len(fib) - 1  # the classic worst case: a chain
+    # total weight 2B <= 8192 symbols per block: F(20) = 6765 <= 8192 < F(21), so <= 18
+    assert sum(fib[:18]) <= 8192
+
+
+def test_huffman_tie_break_leaf_first():
+    # equal weights: leaf queue first; (1,1,2): merge leaves 1+1 -> 2; then leaf 2 first.
+    L = oracle.huffman_lengths(np.array([1, 1, 2], dtype=np.uint32), np.array([5, 6, 7], dtype=np.uint32))
+    assert list(L) == [2, 2, 1]
+    L = oracle.huffman_lengths(np.array([2, 2, 2, 2], dtype=np.uint32))
+    assert list(L) == [2, 2, 2, 2]
+
+
+def parse_stream(s, b, dtype):
+    mode, dt, bl, param, nverb, D = struct.unpack_from("<BBBBHH", s, 0)
+    assert dt == dtype and bl == b
+    out = dict(mode=mode, param=param, nverb=nverb, D=D)
+    if mode == oracle.MODE_HUFF:
+        pbits, total = struct.unpack_from("<II", s, 8)
+        assert total == len(s)
+        off = 16
+        counts = struct.unpack_from("<%dH" % param, s, off)
+        off += (2 * param + 3) // 4 * 4
+        syms = struct.unpack_from("<%dH" % D, s, off)
+        off += (2 * D + 3) // 4 * 4
+        C = (2 << b) // 64
+        chunks = struct.unpack_from("<%dH" % C, s, off)
+        assert sum(chunks) == pbits
+        out.update(counts=counts, syms=syms, pbits=pbits)
+    return out
+
+
+def test_canonical_code_structure():
+    rng = np.random.default_rng(5)
+    for kind in ["normal", "qft", "walsh"]:
+        v = gen_block(kind, 12, rng, oracle.C128)
+        s, info = oracle.compress_block(v, 12, oracle.C128, 1e-6)
+        p = parse_stream(s, 12, oracle.C128)
+        if p["mode"] != oracle.MODE_HUFF:
+            continue
+        counts, syms = p["counts"], p["syms"]
+        assert sum(counts) == p["D"] == info["n_distinct"]
+        # symbols ascending within each length (canonical order)
+        i = 0
+        codes = []
+        code = 0
+        prev = None
+        for L, c in enumerate(counts, start=1):
+            assert list(syms[i:i + c]) == sorted(syms[i:i + c])
+            for _ in range(c):
+                if prev is not None:
+                    code = (code + 1) << (L - prev)
+                codes.append((code, L))
+                prev = L
+            i += c
+        # prefix-free, and a complete code when D >= 2
+        for a in range(len(codes)):
+            for bb in range(len(codes)):
+                if a != bb and codes[a][1] <= codes[bb][1]:
+                    assert codes[bb][0] >> (codes[bb][1] - codes[a][1]) != codes[a][0]
+        if len(codes) >= 2:
+            assert sum(2.0 ** -L for _, L in codes) == 1.0
+
+
+def test_const_header_fields():
+    # eb = 2^-11: 2eb = 2^-10 and r = 2^10 exactly, so the codes are exact integers
+    eb = 2.0 ** -11
+    v = np.full(1 << 8, 0.125 - 0.25j)
+    s, _ = oracle.compress_block(v, 8, oracle.C128, eb)
+    mode, dt, bl, param, nverb, D, qre, qim = struct.unpack("<BBBBHHii", s)
+    assert (mode, dt, bl, nverb) == (oracle.MODE_CONST, oracle.C128, 8, 0)
+    assert (qre, qim) == (128, -256)
+
+
+def test_round_half_even_ties():
+    eb = 2.0 ** -11
+    two = 2.0 ** -10
+    v = np.array([2.5 * two + 3.5j * two, -2.5 * two - 0.5j * two] * 16)
+    s, info = oracle.compress_block(v, 5, oracle.C128, eb)
+    d = oracle.decompress_block(s, 5, oracle.C128, eb)
+    # ties go to the even code, and |x - x'| == eb exactly is within the bound
+    assert info["n_verbatim"] == 0
+    assert d[0] == 2 * two + 4j * two and d[1] == -2 * two - 0j
