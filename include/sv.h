@@ -1,0 +1,172 @@
+/*
+ * sv.h — C ABI of libsv.so, the GB300 (sm_103a) compressed state-vector simulator.
+ *
+ * The library implements the per-gate slice update of Algorithm 1 of Wu, Di, Cappello,
+ * Finkel, Alexeev and Chong, "Memory-Efficient Quantum Circuit Simulation by Using Lossy
+ * Data Compression" (PMES 2018): the state vector of n qubits (Sec. I: 2^n complex
+ * amplitudes) is kept divided into slices, every slice stored compressed by an SZ-style
+ * error-bounded lossy codec (Sec. II); each gate is applied by decompressing, normalizing,
+ * applying the gate and recompressing every slice (Algorithm 1). On the GPU one kernel
+ * launch performs this for all slices at once; decompressed amplitudes live only in
+ * shared memory and registers.
+ *
+ * Conventions
+ *   - Qubit q is bit q of the amplitude index (little-endian).
+ *   - A slice is 2^slice_log2 consecutive amplitudes; it is coded as 2^(slice_log2 -
+ *     block_log2) independent blocks of B = 2^block_log2 amplitudes (the parallel unit).
+ *   - Amplitudes are interleaved (re, im): complex128 (SV_C128, FP64 gate arithmetic) or
+ *     complex64 (SV_C64, FP32 gate arithmetic; quantization and the norm stay FP64).
+ *   - Gates: G is a row-major 2^k x 2^k complex matrix given as (re, im) FP64 pairs;
+ *     targets[0] is the least significant bit of G's basis index. Controls are qubits that
+ *     must all be 1; they are disjoint from the targets. G is copied during the call; the
+ *     caller keeps ownership of every host buffer it passes.
+ *   - error_bound > 0 selects the compressed path; error_bound == 0 selects the plain
+ *     (uncompressed) path, the comparison baseline, with the same calls.
+ *   - Device memory: the library allocates none. The caller hands it one device buffer
+ *     (sv_pool_create); every state's arenas, tables and scalars are sub-allocated there.
+ *   - Streams: every call is ordered on the state's CUDA stream (cudaStream_t passed as
+ *     void*, NULL = legacy default stream). Calls that return host data synchronize that
+ *     stream; the others are asynchronous.
+ *   - Errors: every call returns 0 (SV_OK) or a negative SV_ERR_* code. An error raised
+ *     inside a kernel (stream corruption, arena overflow, norm collapse) is recorded on the
+ *     device and returned by the next synchronizing call; later passes of that state are
+ *     skipped until then. Arena overflow is recovered inside sv_sync by growing the arena
+ *     and replaying the logged gates, so callers only see SV_ERR_OOM when the pool is full.
+ */
+#ifndef SV_H
+#define SV_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SV_OK 0
+#define SV_ERR_ARG (-1)         /* invalid argument */
+#define SV_ERR_OOM (-2)         /* pool exhausted */
+#define SV_ERR_CUDA (-3)        /* a CUDA runtime call failed */
+#define SV_ERR_NORM (-4)        /* stored norm is zero or not finite */
+#define SV_ERR_CORRUPT (-5)     /* a block stream failed the decoder's bounds checks */
+#define SV_ERR_UNSUPPORTED (-6) /* outside this build's limits (see each call) */
+#define SV_ERR_TIMEOUT (-7)     /* a bounded device wait ran out */
+#define SV_ERR_INTERNAL (-8)    /* a device-side consistency check failed (a library bug) */
+
+#define SV_C64 1
+#define SV_C128 2
+
+typedef struct sv_pool sv_pool;
+typedef struct sv_state sv_state;
+
+/* Statistics of the most recent gate pass (or of sv_create's initial compression). */
+typedef struct {
+  uint64_t pass_index;       /* passes completed on this state */
+  uint64_t compressed_bytes; /* sum of all block streams (headers, codebooks, payload) */
+  uint64_t table_bytes;      /* block offset/length tables */
+  uint64_t n_blocks;
+  uint64_t blocks_const, blocks_huff, blocks_pack; /* block modes */
+  uint64_t n_verbatim, n_escape;
+  double norm;               /* N of the stored state after the pass */
+  double sigma;              /* scale the next pass applies, 1/sqrt(norm) */
+} sv_stats_t;
+
+/* ---------------------------------------------------------------------------------------
+ * Pool. dev_base: device pointer to `bytes` bytes owned by the caller (e.g. a torch
+ * tensor), 256-byte aligned, valid until sv_pool_destroy. The pool hands out page runs
+ * (2 MiB pages) to states. Returns SV_ERR_ARG on a NULL/misaligned pointer.
+ * ------------------------------------------------------------------------------------- */
+int sv_pool_create(void* dev_base, size_t bytes, sv_pool** out);
+int sv_pool_destroy(sv_pool* pool); /* fails with SV_ERR_ARG while states remain */
+int sv_pool_usage(const sv_pool* pool, size_t* used_bytes, size_t* capacity_bytes);
+
+/* ---------------------------------------------------------------------------------------
+ * sv_create — a state of n_qubits initialized to |0...0>, compressed (Algorithm 1's input;
+ * Sec. II error bound).
+ *   n_qubits   1..40 (compressed: block_log2 <= n_qubits), slice_log2 in [block_log2, n].
+ *   error_bound absolute bound on every real and imaginary part after each compression,
+ *              > 0; or 0 for the plain path (no codec).
+ *   dtype      SV_C64 or SV_C128.
+ *   stream     cudaStream_t (as void*) all work of this state is ordered on.
+ * Block size: min(slice_log2, 12) unless sv_create_ex sets it (5..12; -1 = default).
+ * arena_bytes (sv_create_ex): initial capacity of each of the two arenas (0 = default,
+ *   64 bytes per block, at least one 2 MiB page); arenas grow on overflow (sv_sync).
+ * Returns SV_ERR_OOM when the pool cannot hold the state's initial arenas.
+ * ------------------------------------------------------------------------------------- */
+int sv_create(sv_pool* pool, int n_qubits, int slice_log2, double error_bound, int dtype,
+              void* stream, sv_state** out);
+int sv_create_ex(sv_pool* pool, int n_qubits, int slice_log2, int block_log2,
+                 double error_bound, int dtype, size_t arena_bytes, void* stream,
+                 sv_state** out);
+int sv_destroy(sv_state* s);
+
+/* Re-initialize to the computational basis state |index> (index < 2^n). Asynchronous. */
+int sv_reset_basis(sv_state* s, uint64_t index);
+
+/* ---------------------------------------------------------------------------------------
+ * sv_apply_gate — one gate pass of Algorithm 1 over every slice: Decompress(S),
+ * Normalize(S) (global scale 1/sqrt(N) of the stored norm N), GateComputation(G, S),
+ * Compress(S). Slices are processed in every pass, also where the controls make the gate
+ * the identity. Targets at or above block_log2 pair the 2^h coupled blocks inside one CTA
+ * (h <= 2 in this build: SV_ERR_UNSUPPORTED otherwise). k in 1..3 targets.
+ * Plain path: G applied in place to the uncompressed vector (no normalization).
+ * Asynchronous; errors raised on the device are reported by the next synchronizing call.
+ * ------------------------------------------------------------------------------------- */
+int sv_apply_gate(sv_state* s, const double* G, const int* targets, int k,
+                  const int* controls, int n_controls);
+
+/* Wait for the state's stream, resolve arena overflow (grow + replay) and return any
+ * error recorded on the device. */
+int sv_sync(sv_state* s);
+
+/* ---------------------------------------------------------------------------------------
+ * Measurements (synchronizing).
+ * sv_measure_probs: marginal probabilities of the m (<= 14) given qubits of the normalized
+ *   stored state; out[2^m] (host), out[v] = P(bits of the listed qubits = v, qubits[0]
+ *   least significant).
+ * sv_amplitudes: the stored (reconstructed, not rescaled) amplitudes x' at host indices
+ *   idx[] into out[2*cnt] (re, im FP64). The stored state has norm sv_norm(); multiply by
+ *   1/sqrt(norm) for the normalized amplitudes.
+ * sv_read_amplitudes: stored amplitudes [start, start+count) into host out[2*count].
+ * sv_fidelity: |<a|b>|^2 / (<a|a><b|b>) of two states of equal n (either path).
+ * sv_compressed_bytes: bytes of all block streams of the current state (plain path: the
+ *   vector's bytes).
+ * ------------------------------------------------------------------------------------- */
+int sv_measure_probs(sv_state* s, const int* qubits, int m, double* out);
+int sv_amplitudes(sv_state* s, const uint64_t* idx, size_t cnt, double* out);
+int sv_read_amplitudes(sv_state* s, uint64_t start, uint64_t count, double* out);
+int sv_fidelity(sv_state* a, sv_state* b, double* out);
+int sv_compressed_bytes(sv_state* s, uint64_t* out);
+int sv_stats(sv_state* s, sv_stats_t* out);
+int sv_norm(sv_state* s, double* out);
+
+/* Copy block `b`'s stream (current state) to host `out` (capacity `cap` bytes); *len gets
+ * its length. SV_ERR_ARG when cap is too small. Used to compare streams byte by byte. */
+int sv_block_stream(sv_state* s, uint64_t b, uint8_t* out, size_t cap, size_t* len);
+
+/* ---------------------------------------------------------------------------------------
+ * Standalone block codec (Sec. II), the same device code the gate pass uses.
+ * sv_codec_compress: nblocks blocks of 2^block_log2 amplitudes from device `values`
+ *   (interleaved, dtype's component type) into device `out` (capacity `cap` bytes); block
+ *   i's stream is written at out + offsets[i] with length lengths[i] (device arrays of
+ *   nblocks u64/u32). Streams are packed in an order that is not specified. *used (host)
+ *   receives the total bytes. SV_ERR_OOM when cap is too small (nothing is valid then).
+ * sv_codec_decompress: the inverse, from device streams at in + offsets[i] into device
+ *   `values`. SV_ERR_CORRUPT when a stream fails the bounds checks.
+ * Both synchronize `stream`. The scratch they need (a few counters) is the caller's
+ *   `scratch` device buffer of at least sv_codec_scratch_bytes() bytes.
+ * ------------------------------------------------------------------------------------- */
+size_t sv_codec_scratch_bytes(void);
+int sv_codec_compress(const void* values, uint64_t nblocks, int block_log2, int dtype,
+                      double error_bound, void* out, uint64_t cap, uint64_t* offsets,
+                      uint32_t* lengths, void* scratch, void* stream, uint64_t* used);
+int sv_codec_decompress(const void* in, const uint64_t* offsets, const uint32_t* lengths,
+                        uint64_t nblocks, int block_log2, int dtype, double error_bound,
+                        void* values, void* scratch, void* stream);
+
+/* Library version string and the sm architecture it was built for. */
+const char* sv_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,751 @@
+// sv_api.cu — host side of libsv.so: the C ABI declared in include/sv.h.
+//
+// Memory: the caller's device buffer is the pool (2 MiB pages, first fit). A compressed
+// state owns a metadata run (device scalars, two block tables, per-block verbatim sums,
+// tree scratch) and two arenas (ping-pong: a pass reads one and bump-allocates its output
+// streams in the other). An arena that overflows during a pass poisons the state on the
+// device (later passes return at once); sv_sync grows the arena to the size the pass asked
+// for and replays the logged passes from the failed one, whose input arena is intact.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <vector>
+
+#include "../../include/sv.h"
+#include "sv_internal.h"
+
+using namespace sv;
+
+namespace {
+
+constexpr size_t kPage = 2u << 20;
+
+size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace
+
+struct sv_pool {
+  uint8_t* base = nullptr;
+  size_t bytes = 0;
+  std::map<size_t, size_t> free_runs;  // offset -> length (bytes, page multiples)
+  size_t used = 0;
+  int nstates = 0;
+  std::mutex mu;
+
+  bool alloc(size_t nbytes, size_t* off) {
+    std::lock_guard<std::mutex> g(mu);
+    const size_t need = round_up(nbytes ? nbytes : 1, kPage);
+    for (auto it = free_runs.begin(); it != free_runs.end(); ++it) {
+      if (it->second >= need) {
+        *off = it->first;
+        const size_t rest = it->second - need;
+        const size_t roff = it->first + need;
+        free_runs.erase(it);
+        if (rest) free_runs[roff] = rest;
+        used += need;
+        return true;
+      }
+    }
+    return false;
+  }
+  void release(size_t off, size_t nbytes) {
+    std::lock_guard<std::mutex> g(mu);
+    const size_t len = round_up(nbytes ? nbytes : 1, kPage);
+    used -= len;
+    auto it = free_runs.emplace(off, len).first;
+    auto nx = std::next(it);
+    if (nx != free_runs.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_runs.erase(nx);
+    }
+    if (it != free_runs.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_runs.erase(it);
+      }
+    }
+  }
+};
+
+namespace {
+
+struct Logged {
+  int basis = 0;  // 1: initial compression of |basis_index>
+  unsigned long long basis_index = 0;
+  std::vector<double> G;
+  std::vector<int> targets, controls;
+  unsigned int seq = 0;
+  int in_id = 0, out_id = 1;
+};
+
+struct Region {
+  size_t off = 0, bytes = 0;
+  bool live = false;
+};
+
+}  // namespace
+
+struct sv_state {
+  sv_pool* pool = nullptr;
+  int n = 0, sl = 0, b = 0, dtype = 2;
+  double eb = 0.0;
+  bool plain = false;
+  QuantP qp{};
+  double two2 = 0.0;
+  cudaStream_t st = nullptr;
+  // plain
+  Region psi_r;
+  void* psi = nullptr;
+  // compressed
+  unsigned long long nblocks = 0;
+  Region meta_r, arena_r[2], aux_r;
+  DevScalars* sc = nullptr;
+  unsigned long long* toff[2] = {nullptr, nullptr};
+  unsigned int* tlen[2] = {nullptr, nullptr};
+  double* vsum = nullptr;
+  double* tree = nullptr;
+  double* vroot = nullptr;
+  uint8_t* arena[2] = {nullptr, nullptr};
+  int cur = 0;
+  unsigned int seq = 0;
+  std::vector<Logged> log;
+  // measurement scratch
+  double* chunk[2] = {nullptr, nullptr};
+  double* bins = nullptr;
+  double* acc = nullptr;
+  int* qdev = nullptr;
+  unsigned long long chunk_amps = 0;
+  int sticky_err = 0;
+};
+
+namespace {
+
+int cuda_err(cudaError_t e) {
+  if (e == cudaSuccess) return SV_OK;
+  std::fprintf(stderr, "libsv: CUDA error %s\n", cudaGetErrorString(e));
+  return SV_ERR_CUDA;
+}
+
+uint8_t* pool_ptr(sv_pool* p, size_t off) { return p->base + off; }
+
+bool region_alloc(sv_pool* p, Region* r, size_t bytes) {
+  if (!p->alloc(bytes, &r->off)) return false;
+  r->bytes = bytes;
+  r->live = true;
+  return true;
+}
+
+void region_free(sv_pool* p, Region* r) {
+  if (r->live) p->release(r->off, r->bytes);
+  r->live = false;
+}
+
+int status_to_err(unsigned int st) {
+  if (st & kStInternal) return SV_ERR_INTERNAL;
+  if (st & kStCorrupt) return SV_ERR_CORRUPT;
+  if (st & kStNorm) return SV_ERR_NORM;
+  if (st & kStVerbatim) return SV_ERR_UNSUPPORTED;
+  if (st & kStTimeout) return SV_ERR_TIMEOUT;
+  if (st & kStOverflow) return SV_ERR_OOM;
+  return SV_OK;
+}
+
+bool gate_args_ok(const sv_state* s, const int* targets, int k, const int* controls, int nc) {
+  if (!targets || k < 1 || k > 3 || nc < 0 || (nc > 0 && !controls)) return false;
+  unsigned long long seen = 0;
+  for (int l = 0; l < k; ++l) {
+    if (targets[l] < 0 || targets[l] >= s->n || ((seen >> targets[l]) & 1ull)) return false;
+    seen |= 1ull << targets[l];
+  }
+  for (int l = 0; l < nc; ++l) {
+    if (controls[l] < 0 || controls[l] >= s->n || ((seen >> controls[l]) & 1ull)) return false;
+    seen |= 1ull << controls[l];
+  }
+  return true;
+}
+
+// Build the pass arguments of one logged step and launch pass + norm tree + finalize.
+int launch_logged(sv_state* s, const Logged& lg) {
+  PassArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.b = s->b;
+  a.nv = 2 << s->b;
+  a.qp = s->qp;
+  a.two2 = s->two2;
+  a.sc = s->sc;
+  a.vsum = s->vsum;
+  a.seq = lg.seq;
+  a.in_arena = s->arena[lg.in_id];
+  a.in_off = s->toff[lg.in_id];
+  a.in_len = s->tlen[lg.in_id];
+  a.out_arena = s->arena[lg.out_id];
+  a.out_cap = s->arena_r[lg.out_id].bytes;
+  a.out_id = lg.out_id;
+  a.out_off = s->toff[lg.out_id];
+  a.out_len = s->tlen[lg.out_id];
+  if (lg.basis) {
+    a.input_basis = 1;
+    a.basis = lg.basis_index;
+    a.apply_gate = 0;
+    a.use_sigma = 0;
+    a.k = 0;
+    a.K = 1;
+    a.G = 1;
+    a.h = 0;
+    a.nlow = 0;
+    a.pos_delta[0] = 0;
+  } else {
+    const int k = (int)lg.targets.size();
+    a.k = k;
+    a.K = 1 << k;
+    a.apply_gate = 1;
+    a.use_sigma = 1;
+    int lows[5], nl = 0, highs[5], nh = 0;
+    int hidx[5];
+    for (int l = 0; l < k; ++l) {
+      const int t = lg.targets[l];
+      if (t < s->b) lows[nl++] = t;
+      else {
+        hidx[l] = nh;
+        highs[nh++] = t - s->b;
+      }
+    }
+    a.nlow = nl;
+    a.h = nh;
+    a.G = 1 << nh;
+    std::vector<int> ls(lows, lows + nl), hs(highs, highs + nh);
+    std::sort(ls.begin(), ls.end());
+    std::sort(hs.begin(), hs.end());
+    for (int l = 0; l < nl; ++l) a.low_t[l] = ls[l];
+    for (int l = 0; l < nh; ++l) a.high_pos[l] = hs[l];
+    for (int l = 0; l < nh; ++l) a.slot_shift[l] = highs[l];
+    for (int m = 0; m < a.K; ++m) {
+      int slot = 0, off = 0;
+      for (int l = 0; l < k; ++l) {
+        if (!((m >> l) & 1)) continue;
+        const int t = lg.targets[l];
+        if (t < s->b) off |= 1 << t;
+        else slot |= 1 << hidx[l];
+      }
+      a.pos_delta[m] = slot * a.nv + 2 * off;
+    }
+    unsigned long long cm = 0;
+    for (int c : lg.controls) cm |= 1ull << c;
+    a.cmask = cm;
+    for (int e = 0; e < 2 * a.K * a.K; ++e) {
+      a.g[e] = lg.G[e];
+      a.gf[e] = (float)lg.G[e];
+    }
+  }
+  a.ngroups = s->nblocks >> a.h;
+  cudaError_t e = launch_pass(a, s->dtype == SV_C64 ? 1 : 2, s->st);
+  if (e != cudaSuccess) return cuda_err(e);
+  e = launch_vsum_tree(s->vsum, s->nblocks, s->tree, s->vroot, s->sc, s->st);
+  if (e != cudaSuccess) return cuda_err(e);
+  e = launch_finalize(s->sc, s->vroot, s->two2, lg.in_id, lg.seq, s->st);
+  return cuda_err(e);
+}
+
+int submit(sv_state* s, Logged lg) {
+  lg.seq = s->seq++;
+  lg.in_id = s->cur;
+  lg.out_id = s->cur ^ 1;
+  int rc = launch_logged(s, lg);
+  if (rc) return rc;
+  s->cur ^= 1;
+  s->log.push_back(std::move(lg));
+  if (s->log.size() >= 256) return sv_sync(s);
+  return SV_OK;
+}
+
+int read_scalars(sv_state* s, DevScalars* h) {
+  cudaError_t e = cudaMemcpyAsync(h, s->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, s->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+  return cuda_err(e);
+}
+
+int grow_arena(sv_state* s, int id, size_t need) {
+  size_t want = std::max(s->arena_r[id].bytes * 2, need + need / 4);
+  region_free(s->pool, &s->arena_r[id]);
+  if (!region_alloc(s->pool, &s->arena_r[id], want)) {
+    if (!region_alloc(s->pool, &s->arena_r[id], need)) return SV_ERR_OOM;
+  }
+  s->arena[id] = pool_ptr(s->pool, s->arena_r[id].off);
+  return SV_OK;
+}
+
+int ensure_aux(sv_state* s) {
+  if (s->aux_r.live) return SV_OK;
+  const unsigned long long dim = 1ull << s->n;
+  s->chunk_amps = std::min<unsigned long long>(dim, 1ull << 20);
+  const size_t chunk_bytes = (size_t)s->chunk_amps * 16;
+  const size_t bytes = 2 * chunk_bytes + (sizeof(double) << 16) + 64 + 4096;
+  if (!region_alloc(s->pool, &s->aux_r, bytes)) return SV_ERR_OOM;
+  uint8_t* p = pool_ptr(s->pool, s->aux_r.off);
+  s->chunk[0] = (double*)p;
+  s->chunk[1] = (double*)(p + chunk_bytes);
+  s->bins = (double*)(p + 2 * chunk_bytes);
+  s->acc = (double*)(p + 2 * chunk_bytes + (sizeof(double) << 16));
+  s->qdev = (int*)(p + 2 * chunk_bytes + (sizeof(double) << 16) + 64);
+  return SV_OK;
+}
+
+// Decoded FP64 amplitudes [start, start+count) (count <= chunk_amps) into dst (device).
+int read_chunk(sv_state* s, unsigned long long start, unsigned long long count, double* dst) {
+  if (s->plain) return cuda_err(launch_plain_read(s->psi, s->dtype == SV_C64 ? 1 : 2, start, count, dst, s->st));
+  const unsigned long long B = 1ull << s->b;
+  const unsigned long long b0 = start / B, b1 = (start + count + B - 1) / B;
+  // chunk sizes are multiples of B (start, count aligned by the callers)
+  cudaError_t e = launch_read_blocks(s->arena[s->cur], s->toff[s->cur], s->tlen[s->cur], b0, b1 - b0,
+                                     s->b, s->dtype == SV_C64 ? 1 : 2, s->qp, dst, s->sc, s->st);
+  return cuda_err(e);
+}
+
+int check_status(sv_state* s) {
+  DevScalars h;
+  int rc = read_scalars(s, &h);
+  if (rc) return rc;
+  return status_to_err(h.status);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sv_version(void) { return "libsv 0.1 (sm_103a)"; }
+
+int sv_pool_create(void* dev_base, size_t bytes, sv_pool** out) {
+  if (!dev_base || !out || ((uintptr_t)dev_base & 255) || bytes < kPage) return SV_ERR_ARG;
+  sv_pool* p = new sv_pool();
+  p->base = (uint8_t*)dev_base;
+  p->bytes = bytes / kPage * kPage;
+  p->free_runs[0] = p->bytes;
+  *out = p;
+  return SV_OK;
+}
+
+int sv_pool_destroy(sv_pool* p) {
+  if (!p) return SV_ERR_ARG;
+  if (p->nstates) return SV_ERR_ARG;
+  delete p;
+  return SV_OK;
+}
+
+int sv_pool_usage(const sv_pool* p, size_t* used, size_t* cap) {
+  if (!p) return SV_ERR_ARG;
+  if (used) *used = p->used;
+  if (cap) *cap = p->bytes;
+  return SV_OK;
+}
+
+int sv_create_ex(sv_pool* pool, int n, int sl, int bl, double eb, int dtype, size_t arena_bytes,
+                 void* stream, sv_state** out) {
+  if (!pool || !out || n < 1 || n > 40 || (dtype != SV_C64 && dtype != SV_C128) || !(eb >= 0.0) ||
+      !std::isfinite(eb))
+    return SV_ERR_ARG;
+  sv_state* s = new sv_state();
+  s->pool = pool;
+  s->n = n;
+  s->dtype = dtype;
+  s->eb = eb;
+  s->st = (cudaStream_t)stream;
+  s->plain = eb == 0.0;
+  if (s->plain) {
+    s->sl = sl;
+    const size_t bytes = (size_t)(dtype == SV_C64 ? 8 : 16) << n;
+    if (!region_alloc(pool, &s->psi_r, bytes)) {
+      delete s;
+      return SV_ERR_OOM;
+    }
+    s->psi = pool_ptr(pool, s->psi_r.off);
+    pool->nstates++;
+    int rc = cuda_err(launch_plain_basis(s->psi, n, dtype == SV_C64 ? 1 : 2, 0, s->st));
+    *out = s;
+    return rc;
+  }
+  if (bl < 0) bl = std::min(sl, 12);
+  if (bl < 5 || bl > 12 || bl > n || sl < bl || sl > n) {
+    delete s;
+    return SV_ERR_ARG;
+  }
+  s->sl = sl;
+  s->b = bl;
+  s->qp.eb = eb;
+  s->qp.two = 2.0 * eb;
+  s->qp.r = 1.0 / s->qp.two;
+  s->two2 = s->qp.two * s->qp.two;
+  s->nblocks = 1ull << (n - bl);
+  // metadata run: scalars | table 0 | table 1 | vsum | tree scratch | root
+  const size_t nb = s->nblocks;
+  size_t off = 0;
+  const size_t o_sc = off;
+  off += round_up(sizeof(DevScalars), 256);
+  const size_t o_off0 = off;
+  off += round_up(nb * 8, 256);
+  const size_t o_off1 = off;
+  off += round_up(nb * 8, 256);
+  const size_t o_len0 = off;
+  off += round_up(nb * 4, 256);
+  const size_t o_len1 = off;
+  off += round_up(nb * 4, 256);
+  const size_t o_vsum = off;
+  off += round_up(nb * 8, 256);
+  const size_t o_tree = off;
+  off += round_up(2 * (nb / 2048 + 1) * 8, 256);
+  const size_t o_root = off;
+  off += 256;
+  if (!region_alloc(pool, &s->meta_r, off)) {
+    delete s;
+    return SV_ERR_OOM;
+  }
+  uint8_t* m = pool_ptr(pool, s->meta_r.off);
+  s->sc = (DevScalars*)(m + o_sc);
+  s->toff[0] = (unsigned long long*)(m + o_off0);
+  s->toff[1] = (unsigned long long*)(m + o_off1);
+  s->tlen[0] = (unsigned int*)(m + o_len0);
+  s->tlen[1] = (unsigned int*)(m + o_len1);
+  s->vsum = (double*)(m + o_vsum);
+  s->tree = (double*)(m + o_tree);
+  s->vroot = (double*)(m + o_root);
+  // arenas: the initial state is nearly all 16-byte CONST blocks
+  const size_t init_cap = arena_bytes ? arena_bytes : std::max<size_t>(kPage, nb * 64);
+  for (int id = 0; id < 2; ++id) {
+    if (!region_alloc(pool, &s->arena_r[id], init_cap)) {
+      region_free(pool, &s->arena_r[0]);
+      region_free(pool, &s->meta_r);
+      delete s;
+      return SV_ERR_OOM;
+    }
+    s->arena[id] = pool_ptr(pool, s->arena_r[id].off);
+  }
+  pool->nstates++;
+  *out = s;
+  return sv_reset_basis(s, 0);
+}
+
+int sv_create(sv_pool* pool, int n, int sl, double eb, int dtype, void* stream, sv_state** out) {
+  return sv_create_ex(pool, n, sl, -1, eb, dtype, 0, stream, out);
+}
+
+int sv_destroy(sv_state* s) {
+  if (!s) return SV_ERR_ARG;
+  cudaStreamSynchronize(s->st);
+  region_free(s->pool, &s->psi_r);
+  region_free(s->pool, &s->meta_r);
+  region_free(s->pool, &s->arena_r[0]);
+  region_free(s->pool, &s->arena_r[1]);
+  region_free(s->pool, &s->aux_r);
+  s->pool->nstates--;
+  delete s;
+  return SV_OK;
+}
+
+int sv_reset_basis(sv_state* s, uint64_t index) {
+  if (!s || (index >> s->n)) return SV_ERR_ARG;
+  if (s->plain) return cuda_err(launch_plain_basis(s->psi, s->n, s->dtype == SV_C64 ? 1 : 2, index, s->st));
+  DevScalars h;
+  std::memset(&h, 0, sizeof(h));
+  h.fail_seq = 0xFFFFFFFFu;
+  h.sigma = 1.0;
+  h.norm = 1.0;
+  cudaError_t e = cudaMemcpyAsync(s->sc, &h, sizeof(h), cudaMemcpyHostToDevice, s->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);  // h is a stack buffer
+  if (e != cudaSuccess) return cuda_err(e);
+  s->log.clear();
+  s->sticky_err = 0;
+  Logged lg;
+  lg.basis = 1;
+  lg.basis_index = index;
+  return submit(s, std::move(lg));
+}
+
+int sv_apply_gate(sv_state* s, const double* G, const int* targets, int k, const int* controls,
+                  int nc) {
+  if (!s || !G || !gate_args_ok(s, targets, k, controls, nc)) return SV_ERR_ARG;
+  if (s->plain) {
+    unsigned long long cm = 0;
+    for (int l = 0; l < nc; ++l) cm |= 1ull << controls[l];
+    return cuda_err(launch_plain_gate(s->psi, s->n, s->dtype == SV_C64 ? 1 : 2, G, targets, k, cm, s->st));
+  }
+  int nh = 0;
+  for (int l = 0; l < k; ++l) nh += targets[l] >= s->b;
+  if (nh > 2) return SV_ERR_UNSUPPORTED;
+  Logged lg;
+  lg.G.assign(G, G + 2 * (1 << k) * (1 << k));
+  lg.targets.assign(targets, targets + k);
+  if (nc) lg.controls.assign(controls, controls + nc);
+  return submit(s, std::move(lg));
+}
+
+int sv_sync(sv_state* s) {
+  if (!s) return SV_ERR_ARG;
+  if (s->plain) return cuda_err(cudaStreamSynchronize(s->st));
+  for (int attempt = 0; attempt < 64; ++attempt) {
+    DevScalars h;
+    int rc = read_scalars(s, &h);
+    if (rc) return rc;
+    if (h.status == 0) {
+      s->log.clear();
+      return SV_OK;
+    }
+    if (h.status != kStOverflow) return status_to_err(h.status);
+    // find the failed pass in the log
+    size_t i = 0;
+    while (i < s->log.size() && s->log[i].seq != h.fail_seq) ++i;
+    if (i == s->log.size()) return SV_ERR_OOM;
+    const Logged& f = s->log[i];
+    rc = grow_arena(s, f.out_id, (size_t)h.bump[f.out_id]);
+    if (rc) return rc;
+    h.status = 0;
+    h.fail_seq = 0xFFFFFFFFu;
+    h.bump[f.out_id] = 0;
+    std::memset(&h.acc, 0, sizeof(h.acc));
+    cudaError_t e = cudaMemcpyAsync(s->sc, &h, sizeof(h), cudaMemcpyHostToDevice, s->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+    if (e != cudaSuccess) return cuda_err(e);
+    for (size_t j = i; j < s->log.size(); ++j) {
+      rc = launch_logged(s, s->log[j]);
+      if (rc) return rc;
+    }
+  }
+  return SV_ERR_OOM;
+}
+
+int sv_norm(sv_state* s, double* out) {
+  if (!s || !out) return SV_ERR_ARG;
+  int rc = sv_sync(s);
+  if (rc) return rc;
+  if (s->plain) {
+    // plain norm via a dot of the state with itself
+    rc = ensure_aux(s);
+    if (rc) return rc;
+    cudaMemsetAsync(s->acc, 0, 4 * sizeof(double), s->st);
+    const unsigned long long dim = 1ull << s->n;
+    for (unsigned long long st = 0; st < dim; st += s->chunk_amps) {
+      rc = read_chunk(s, st, s->chunk_amps, s->chunk[0]);
+      if (rc) return rc;
+      cudaError_t e = launch_dot_chunk(s->chunk[0], s->chunk[0], s->chunk_amps, s->acc, s->st);
+      if (e != cudaSuccess) return cuda_err(e);
+    }
+    double h[4];
+    cudaMemcpyAsync(h, s->acc, sizeof(h), cudaMemcpyDeviceToHost, s->st);
+    cudaStreamSynchronize(s->st);
+    *out = h[2];
+    return SV_OK;
+  }
+  DevScalars h;
+  rc = read_scalars(s, &h);
+  if (rc) return rc;
+  *out = h.norm;
+  return SV_OK;
+}
+
+int sv_stats(sv_state* s, sv_stats_t* out) {
+  if (!s || !out) return SV_ERR_ARG;
+  int rc = sv_sync(s);
+  if (rc) return rc;
+  std::memset(out, 0, sizeof(*out));
+  if (s->plain) {
+    out->compressed_bytes = (uint64_t)(s->dtype == SV_C64 ? 8 : 16) << s->n;
+    return SV_OK;
+  }
+  DevScalars h;
+  rc = read_scalars(s, &h);
+  if (rc) return rc;
+  out->pass_index = h.pass_index;
+  out->compressed_bytes = h.last_bytes;
+  out->table_bytes = s->nblocks * 12;
+  out->n_blocks = s->nblocks;
+  out->blocks_const = h.last.modes[0];
+  out->blocks_huff = h.last.modes[1];
+  out->blocks_pack = h.last.modes[2];
+  out->n_verbatim = h.last.n_verbatim;
+  out->n_escape = h.last.n_escape;
+  out->norm = h.norm;
+  out->sigma = h.sigma;
+  return SV_OK;
+}
+
+int sv_compressed_bytes(sv_state* s, uint64_t* out) {
+  if (!s || !out) return SV_ERR_ARG;
+  sv_stats_t st;
+  int rc = sv_stats(s, &st);
+  if (rc) return rc;
+  *out = st.compressed_bytes;
+  return SV_OK;
+}
+
+int sv_block_stream(sv_state* s, uint64_t b, uint8_t* out, size_t cap, size_t* len) {
+  if (!s || s->plain || b >= s->nblocks || !len) return SV_ERR_ARG;
+  int rc = sv_sync(s);
+  if (rc) return rc;
+  unsigned long long off = 0;
+  unsigned int l = 0;
+  cudaMemcpyAsync(&off, s->toff[s->cur] + b, 8, cudaMemcpyDeviceToHost, s->st);
+  cudaMemcpyAsync(&l, s->tlen[s->cur] + b, 4, cudaMemcpyDeviceToHost, s->st);
+  cudaError_t e = cudaStreamSynchronize(s->st);
+  if (e != cudaSuccess) return cuda_err(e);
+  *len = l;
+  if (!out) return SV_OK;
+  if (cap < l) return SV_ERR_ARG;
+  e = cudaMemcpy(out, s->arena[s->cur] + off, l, cudaMemcpyDeviceToHost);
+  return cuda_err(e);
+}
+
+int sv_read_amplitudes(sv_state* s, uint64_t start, uint64_t count, double* out) {
+  if (!s || !out || start + count > (1ull << s->n) || start + count < start) return SV_ERR_ARG;
+  int rc = sv_sync(s);
+  if (rc) return rc;
+  rc = ensure_aux(s);
+  if (rc) return rc;
+  const unsigned long long B = s->plain ? 1 : (1ull << s->b);
+  unsigned long long pos = start;
+  const unsigned long long end = start + count;
+  while (pos < end) {
+    const unsigned long long c0 = pos / B * B;  // aligned chunk start
+    unsigned long long c1 = std::min<unsigned long long>(c0 + s->chunk_amps, 1ull << s->n);
+    rc = read_chunk(s, c0, c1 - c0, s->chunk[0]);
+    if (rc) return rc;
+    const unsigned long long take = std::min(c1, end) - pos;
+    cudaError_t e = cudaMemcpyAsync(out + 2 * (pos - start), s->chunk[0] + 2 * (pos - c0), take * 16,
+                                    cudaMemcpyDeviceToHost, s->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+    if (e != cudaSuccess) return cuda_err(e);
+    pos += take;
+  }
+  return s->plain ? SV_OK : check_status(s);
+}
+
+int sv_amplitudes(sv_state* s, const uint64_t* idx, size_t cnt, double* out) {
+  if (!s || (cnt && (!idx || !out))) return SV_ERR_ARG;
+  for (size_t i = 0; i < cnt; ++i) {
+    int rc = sv_read_amplitudes(s, idx[i], 1, out + 2 * i);
+    if (rc) return rc;
+  }
+  return SV_OK;
+}
+
+int sv_measure_probs(sv_state* s, const int* qubits, int m, double* out) {
+  if (!s || !qubits || !out || m < 1 || m > 14) return SV_ERR_ARG;
+  for (int l = 0; l < m; ++l)
+    if (qubits[l] < 0 || qubits[l] >= s->n) return SV_ERR_ARG;
+  int rc = sv_sync(s);
+  if (rc) return rc;
+  rc = ensure_aux(s);
+  if (rc) return rc;
+  cudaMemsetAsync(s->bins, 0, sizeof(double) << m, s->st);
+  int qh[16];
+  for (int l = 0; l < m; ++l) qh[l] = qubits[l];
+  cudaMemcpyAsync(s->qdev, qh, sizeof(int) * m, cudaMemcpyHostToDevice, s->st);
+  const unsigned long long dim = 1ull << s->n;
+  for (unsigned long long st = 0; st < dim; st += s->chunk_amps) {
+    rc = read_chunk(s, st, s->chunk_amps, s->chunk[0]);
+    if (rc) return rc;
+    cudaError_t e = launch_probs_chunk(s->chunk[0], st, s->chunk_amps, s->qdev, m, s->bins, s->st);
+    if (e != cudaSuccess) return cuda_err(e);
+  }
+  std::vector<double> h((size_t)1 << m);
+  cudaError_t e = cudaMemcpyAsync(h.data(), s->bins, sizeof(double) << m, cudaMemcpyDeviceToHost, s->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+  if (e != cudaSuccess) return cuda_err(e);
+  double tot = 0.0;
+  for (double v : h) tot += v;
+  if (!(tot > 0.0)) return SV_ERR_NORM;
+  for (size_t i = 0; i < h.size(); ++i) out[i] = h[i] / tot;
+  return s->plain ? SV_OK : check_status(s);
+}
+
+int sv_fidelity(sv_state* a, sv_state* b, double* out) {
+  if (!a || !b || !out || a->n != b->n) return SV_ERR_ARG;
+  int rc = sv_sync(a);
+  if (!rc && b != a) rc = sv_sync(b);
+  if (rc) return rc;
+  rc = ensure_aux(a);
+  if (!rc) rc = ensure_aux(b);
+  if (rc) return rc;
+  // work on a's stream; b's reads are ordered after b's own work by the sync above
+  const unsigned long long dim = 1ull << a->n;
+  const unsigned long long ch = std::min(a->chunk_amps, b->chunk_amps);
+  cudaMemsetAsync(a->acc, 0, 4 * sizeof(double), a->st);
+  for (unsigned long long st = 0; st < dim; st += ch) {
+    rc = read_chunk(a, st, ch, a->chunk[0]);
+    if (rc) return rc;
+    cudaStream_t keep = b->st;
+    b->st = a->st;
+    rc = read_chunk(b, st, ch, a->chunk[1]);
+    b->st = keep;
+    if (rc) return rc;
+    cudaError_t e = launch_dot_chunk(a->chunk[0], a->chunk[1], ch, a->acc, a->st);
+    if (e != cudaSuccess) return cuda_err(e);
+  }
+  double h[4];
+  cudaError_t e = cudaMemcpyAsync(h, a->acc, sizeof(h), cudaMemcpyDeviceToHost, a->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(a->st);
+  if (e != cudaSuccess) return cuda_err(e);
+  if (!(h[2] > 0.0) || !(h[3] > 0.0)) return SV_ERR_NORM;
+  *out = (h[0] * h[0] + h[1] * h[1]) / (h[2] * h[3]);
+  if (!a->plain && (rc = check_status(a))) return rc;
+  if (!b->plain && (rc = check_status(b))) return rc;
+  return SV_OK;
+}
+
+size_t sv_codec_scratch_bytes(void) { return round_up(sizeof(DevScalars), 256); }
+
+int sv_codec_compress(const void* values, uint64_t nblocks, int bl, int dtype, double eb, void* out,
+                      uint64_t cap, uint64_t* offsets, uint32_t* lengths, void* scratch,
+                      void* stream, uint64_t* used) {
+  if (!values || !out || !offsets || !lengths || !scratch || bl < 5 || bl > 12 ||
+      (dtype != SV_C64 && dtype != SV_C128) || !(eb > 0.0) || !std::isfinite(eb) ||
+      ((uintptr_t)out & 15) || ((uintptr_t)scratch & 15))
+    return SV_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  DevScalars* sc = (DevScalars*)scratch;
+  QuantP qp;
+  qp.eb = eb;
+  qp.two = 2.0 * eb;
+  qp.r = 1.0 / qp.two;
+  cudaError_t e = cudaMemsetAsync(sc, 0, sizeof(DevScalars), st);
+  if (e != cudaSuccess) return cuda_err(e);
+  e = launch_codec_compress(values, nblocks, bl, dtype == SV_C64 ? 1 : 2, qp, (uint8_t*)out, cap,
+                            (unsigned long long*)offsets, lengths, sc, nullptr, st);
+  if (e != cudaSuccess) return cuda_err(e);
+  DevScalars h;
+  e = cudaMemcpyAsync(&h, sc, sizeof(h), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_err(e);
+  if (used) *used = h.bump[0];
+  return status_to_err(h.status);
+}
+
+int sv_codec_decompress(const void* in, const uint64_t* offsets, const uint32_t* lengths,
+                        uint64_t nblocks, int bl, int dtype, double eb, void* values, void* scratch,
+                        void* stream) {
+  if (!in || !offsets || !lengths || !values || !scratch || bl < 5 || bl > 12 ||
+      (dtype != SV_C64 && dtype != SV_C128) || !(eb > 0.0) || !std::isfinite(eb) ||
+      ((uintptr_t)in & 15) || ((uintptr_t)scratch & 15))
+    return SV_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  DevScalars* sc = (DevScalars*)scratch;
+  QuantP qp;
+  qp.eb = eb;
+  qp.two = 2.0 * eb;
+  qp.r = 1.0 / qp.two;
+  cudaError_t e = cudaMemsetAsync(sc, 0, sizeof(DevScalars), st);
+  if (e != cudaSuccess) return cuda_err(e);
+  e = launch_codec_decompress((const uint8_t*)in, (const unsigned long long*)offsets, lengths, nblocks,
+                              bl, dtype == SV_C64 ? 1 : 2, qp, values, sc, st);
+  if (e != cudaSuccess) return cuda_err(e);
+  DevScalars h;
+  e = cudaMemcpyAsync(&h, sc, sizeof(h), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_err(e);
+  return status_to_err(h.status);
+}
+
+}  // extern "C"

@@ -1,0 +1,778 @@
+// sv_block.cuh — one CTA's work on a group of codec blocks: decode, transform, encode.
+//
+// Algorithm 1 of Wu et al. (PMES 2018) processes, for every gate, every slice in four
+// steps: Decompress(S), Normalize(S), GateComputation(G, S), Compress(S). On the GPU a
+// slice is cut into independent blocks of B = 2^b amplitudes and one CTA owns the 2^h
+// blocks that a gate couples (h = number of targets >= b). The decompressed amplitudes
+// never leave shared memory: the integer codes q (one int32 per real value) are decoded
+// into shared memory, the gate is applied tuple by tuple, the results are re-quantized in
+// place, and the new stream is assembled in shared memory and copied out with 16-byte
+// stores into a bump-allocated output arena.
+#pragma once
+#include "sv_device.cuh"
+
+namespace sv {
+
+// Per-CTA scalars in the misc area.
+struct Misc {
+  uint32_t scan[40];
+  unsigned long long red[40];
+  int vin_cnt[4], vout_cnt[4];
+  unsigned int err;
+  int D;
+  int nesc;
+  int cnt;
+  int mode, lmax, width;
+  uint32_t pbits;
+  uint32_t size;
+  unsigned long long out_off;
+  int ok;
+  int first[34];   // canonical first code per length
+  int offs[34];    // first canonical index per length
+  int lcount[34];  // codes per length
+};
+
+// Dynamic shared-memory layout of a worker CTA (host and device agree on it).
+struct Layout {
+  int nv, G, hs, dcap, p2cap;
+  uint32_t off_q, off_vin_pos, off_vin_bits, off_vout_pos, off_vout_bits, off_hkey, off_hval,
+      off_stage, off_build, off_misc, total;
+  uint32_t stage_bytes, build_bytes;
+};
+
+__host__ __device__ inline int next_pow2(int x) {
+  int p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+__host__ __device__ inline Layout make_layout(int b, int G, int csize) {
+  Layout L;
+  L.nv = 2 << b;
+  L.G = G;
+  L.hs = L.nv * 2 < kHashSlots ? L.nv * 2 : kHashSlots;
+  L.dcap = L.nv < kHuffMaxD ? L.nv : kHuffMaxD;
+  L.p2cap = next_pow2(L.dcap);
+  uint32_t o = 0;
+  L.off_q = o;
+  o += (uint32_t)(G * L.nv * 4);
+  L.off_vin_bits = o;
+  o += (uint32_t)(G * kVmax * 8);
+  L.off_vout_bits = o;
+  o += (uint32_t)(G * kVmax * 8);
+  L.off_vin_pos = o;
+  o += (uint32_t)pad_to((size_t)G * kVmax * 2, 16);
+  L.off_vout_pos = o;
+  o += (uint32_t)pad_to((size_t)G * kVmax * 2, 16);
+  L.off_hkey = o;
+  o += (uint32_t)(L.hs * 4);
+  L.off_hval = o;
+  o += (uint32_t)(L.hs * 4);
+  // stream image: header + largest body (PACK at 32 bits) + verbatim section
+  L.stage_bytes = (uint32_t)pad_to(kHdr + (size_t)L.nv * 4 + 2 * kVmax + 8 + (size_t)kVmax * csize + 16, 16);
+  L.off_stage = o;
+  o += L.stage_bytes;
+  // codebook build: keys, vals (p2cap each), internal weights (dcap), parent (2 dcap u16),
+  // lengths (2 dcap u8); decode: LUT (2^kLutBits u32), symbols (dcap u16), chunk starts
+  uint32_t build = (uint32_t)(8 * L.p2cap + 4 * L.dcap + 4 * L.dcap + 2 * L.dcap);
+  uint32_t dec = (uint32_t)(4 * (1 << kLutBits) + 2 * L.dcap + 4 * (L.nv / kChunk + 1));
+  L.build_bytes = (uint32_t)pad_to(build > dec ? build : dec, 16);
+  L.off_build = o;
+  o += L.build_bytes;
+  L.off_misc = o;
+  o += (uint32_t)pad_to(sizeof(Misc), 16);  // scalars and scan workspace
+  L.total = o;
+  return L;
+}
+
+__host__ __device__ inline int worker_threads(int b) {
+  int nv = 2 << b;
+  int t = nv / 2;
+  if (t > 256) t = 256;
+  if (t < 32) t = 32;
+  return t;
+}
+
+struct PassArgs {
+  int b, nv, G, h, k, K, nlow;
+  int low_t[5];       // low targets ascending (for base enumeration)
+  int high_pos[5];    // (high target - b) ascending (block-id expansion)
+  int slot_shift[5];  // for slot bit l (target order of high targets): block-id bit
+  int pos_delta[8];   // value-position offset of tuple member m within the group
+  unsigned long long cmask;
+  int apply_gate;     // 0: identity (initial compression)
+  int input_basis;    // 1: the input is the basis state |basis>
+  unsigned long long basis;
+  int use_sigma;
+  double g[2 * 64];   // gate matrix (re, im), row-major K x K
+  float gf[2 * 64];
+  QuantP qp;
+  double two2;
+  unsigned long long ngroups;
+  const uint8_t* in_arena;
+  const unsigned long long* in_off;
+  const unsigned int* in_len;
+  uint8_t* out_arena;
+  unsigned long long out_cap;
+  int out_id;
+  unsigned long long* out_off;
+  unsigned int* out_len;
+  DevScalars* sc;
+  double* vsum;
+  unsigned int seq;
+};
+
+template <typename Real>
+struct Worker {
+  Layout L;
+  int T, vpt, b;
+  QuantP qp;
+  int32_t* q;
+  uint16_t *vin_pos, *vout_pos;
+  uint64_t *vin_bits, *vout_bits;
+  int *vin_cnt, *vout_cnt;
+  uint32_t *hkey, *hval, *stage;
+  uint8_t* build;
+  Misc* m;
+
+  __device__ void init(unsigned char* smem, const Layout& lay, int b_, const QuantP& p) {
+    L = lay;
+    b = b_;
+    T = blockDim.x;
+    vpt = L.nv / T;
+    qp = p;
+    q = (int32_t*)(smem + L.off_q);
+    vin_bits = (uint64_t*)(smem + L.off_vin_bits);
+    vout_bits = (uint64_t*)(smem + L.off_vout_bits);
+    vin_pos = (uint16_t*)(smem + L.off_vin_pos);
+    vout_pos = (uint16_t*)(smem + L.off_vout_pos);
+    hkey = (uint32_t*)(smem + L.off_hkey);
+    hval = (uint32_t*)(smem + L.off_hval);
+    stage = (uint32_t*)(smem + L.off_stage);
+    build = smem + L.off_build;
+    m = (Misc*)(smem + L.off_misc);
+    vin_cnt = m->vin_cnt;
+    vout_cnt = m->vout_cnt;
+  }
+
+  // ------------------------------------------------------------------------------------
+  // Decompress(S) for one block: stream -> q codes (verbatim slots hold kSentinel and
+  // their raw values go to the vin list). Returns nothing; errors set m->err.
+  // ------------------------------------------------------------------------------------
+  __device__ void decode(int g, const uint8_t* s, uint32_t len) {
+    const int tid = threadIdx.x, nv = L.nv;
+    int32_t* qb = q + g * nv;
+    uint32_t h0 = 0, h1 = 0, h2 = 0, h3 = 0;
+    if (len >= kHdr) {
+      const uint4 hv = __ldg((const uint4*)s);
+      h0 = hv.x;
+      h1 = hv.y;
+      h2 = hv.z;
+      h3 = hv.w;
+    }
+    const int mode = h0 & 0xff, dt = (h0 >> 8) & 0xff, bl = (h0 >> 16) & 0xff, param = h0 >> 24;
+    const int nverb = h1 & 0xffff, D = h1 >> 16;
+    const int want_dt = sizeof(Real) == 8 ? 2 : 1;
+    bool bad = len < kHdr || dt != want_dt || bl != b || mode > kModePack;
+    uint32_t body_end = kHdr;
+    if (!bad && mode == kModeConst) {
+      if (nverb != 0) bad = true;
+      const int32_t qre = (int32_t)h2, qim = (int32_t)h3;
+      for (int j = tid; j < nv; j += T) qb[j] = (j & 1) ? qim : qre;
+      if (tid == 0) vin_cnt[g] = 0;
+      __syncthreads();
+      if (bad && tid == 0) atomicOr(&m->err, kStCorrupt);
+      return;
+    }
+    const uint32_t pbits = h2, total = h3;
+    if (!bad && (total > len || (total & 15))) bad = true;
+    if (!bad && mode == kModePack) {
+      const int width = param;
+      if (width > 32 || pbits != (uint32_t)nv * (uint32_t)width) bad = true;
+      const uint32_t nwords = (pbits + 31) / 32;
+      body_end = kHdr + 4 * nwords;
+      if (body_end > total) bad = true;
+      if (!bad) {
+        const uint32_t* w = (const uint32_t*)(s + kHdr);
+        for (int i = 0; i < vpt; ++i) {
+          const int j = tid * vpt + i;
+          uint32_t z = 0;
+          if (width) z = peek32(w, (uint64_t)j * width, nwords) >> (32 - width);
+          qb[j] = unzigzag(z);
+        }
+      }
+    } else if (!bad && mode == kModeHuff) {
+      const int lmax = param;
+      const int C = nv / kChunk;
+      const uint32_t off_sym = kHdr + (uint32_t)pad_to(2 * lmax, 4);
+      const uint32_t off_chunk = off_sym + (uint32_t)pad_to(2 * D, 4);
+      const uint32_t off_pay = off_chunk + (uint32_t)pad_to(2 * C, 4);
+      const uint32_t nwords = (pbits + 31) / 32;
+      body_end = off_pay + 4 * nwords;
+      if (lmax < 1 || lmax > 24 || D < 1 || D > L.dcap || body_end > total) bad = true;
+      uint32_t* lut = (uint32_t*)build;
+      uint16_t* symtab = (uint16_t*)(build + 4 * (1 << kLutBits));
+      uint32_t* cstart = (uint32_t*)(build + 4 * (1 << kLutBits) + pad_to(2 * L.dcap, 4));
+      if (!bad) {
+        if (tid == 0) {
+          int code = 0, idx = 0;
+          const uint16_t* cnt = (const uint16_t*)(s + kHdr);
+          for (int l = 1; l <= lmax; ++l) {
+            const int c = cnt[l - 1];
+            m->first[l] = code;
+            m->offs[l] = idx;
+            m->lcount[l] = c;
+            code = (code + c) << 1;
+            idx += c;
+          }
+          if (idx != D) atomicOr(&m->err, kStCorrupt);
+        }
+        for (int i = tid; i < D; i += T) symtab[i] = ((const uint16_t*)(s + off_sym))[i];
+        for (int i = tid; i < (1 << kLutBits); i += T) lut[i] = 0;
+      }
+      uint32_t cb = 0;
+      if (!bad && tid < C) cb = ((const uint16_t*)(s + off_chunk))[tid];
+      uint32_t ctot = 0;
+      const uint32_t cs = block_excl_scan_u32(cb, m->scan, &ctot);  // syncs
+      if (!bad && ctot != pbits) bad = true;
+      if (!bad) {
+        if (tid < C) cstart[tid] = cs;
+        if (tid == 0) cstart[C] = pbits;
+        // decode table: every code of length <= kLutBits fills its 2^(kLutBits-l) entries
+        for (int i = tid; i < D; i += T) {
+          int l = 1;
+          while (l < lmax && !(i >= m->offs[l] && i < m->offs[l] + m->lcount[l])) ++l;
+          const uint32_t code = (uint32_t)(m->first[l] + (i - m->offs[l]));
+          if (l <= kLutBits) {
+            const uint32_t lo = code << (kLutBits - l), n = 1u << (kLutBits - l);
+            if (lo + n <= (1u << kLutBits))
+              for (uint32_t e = 0; e < n; ++e) lut[lo + e] = ((uint32_t)(i + 1) << 8) | (uint32_t)l;
+          }
+        }
+      }
+      __syncthreads();
+      if (!bad && tid < C && !m->err) {
+        const uint32_t* w = (const uint32_t*)(s + off_pay);
+        uint64_t pos = cstart[tid];
+        const uint64_t end = cstart[tid + 1];
+        bool cerr = false;
+        for (int i = 0; i < kChunk; ++i) {
+          const uint32_t pk = peek32(w, pos, nwords);
+          const uint32_t e = lut[pk >> (32 - kLutBits)];
+          int idx = -1, l = 0;
+          if (e) {
+            idx = (int)(e >> 8) - 1;
+            l = (int)(e & 0xff);
+          } else {
+            for (l = kLutBits + 1; l <= lmax; ++l) {
+              const int c = (int)(pk >> (32 - l));
+              if (m->lcount[l] && c >= m->first[l] && c - m->first[l] < m->lcount[l]) {
+                idx = m->offs[l] + c - m->first[l];
+                break;
+              }
+            }
+          }
+          if (idx < 0 || idx >= D) {
+            cerr = true;
+            break;
+          }
+          pos += (uint64_t)l;
+          const int sym = symtab[idx];
+          int32_t d;
+          if (sym == 0) {
+            d = (int32_t)peek32(w, pos, nwords);
+            pos += 32;
+          } else {
+            d = sym - 32768;
+          }
+          qb[tid * kChunk + i] = d;
+        }
+        if (cerr || pos != end) atomicOr(&m->err, kStCorrupt);
+      }
+    }
+    if (bad && tid == 0) atomicOr(&m->err, kStCorrupt);
+    __syncthreads();
+    // inverse Lorenzo: q_j = q_{j-2} + delta_j, one running sum per plane
+    int2 loc = make_int2(0, 0);
+    int32_t dv[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i)
+      if (i < vpt) {
+        dv[i] = qb[tid * vpt + i];
+        if (i & 1) loc.y += dv[i];
+        else loc.x += dv[i];
+      }
+    int2 off = block_excl_scan_i2(loc, (int2*)m->red);
+#pragma unroll
+    for (int i = 0; i < 32; ++i)
+      if (i < vpt) {
+        if (i & 1) {
+          off.y += dv[i];
+          qb[tid * vpt + i] = off.y;
+        } else {
+          off.x += dv[i];
+          qb[tid * vpt + i] = off.x;
+        }
+      }
+    __syncthreads();
+    // verbatim section: ascending positions, then raw values (aligned to the value size)
+    if (nverb > kVmax) {
+      if (tid == 0) atomicOr(&m->err, kStVerbatim);
+    } else if (nverb > 0 && !bad) {
+      const uint32_t posoff = body_end;
+      const uint32_t valoff = (uint32_t)pad_to(posoff + 2 * nverb, sizeof(Real));
+      if (valoff + sizeof(Real) * nverb > total) {
+        if (tid == 0) atomicOr(&m->err, kStCorrupt);
+      } else {
+        for (int i = tid; i < nverb; i += T) {
+          const int j = ((const uint16_t*)(s + posoff))[i];
+          uint64_t bits;
+          if (sizeof(Real) == 8) bits = ((const uint64_t*)(s + valoff))[i];
+          else bits = ((const uint32_t*)(s + valoff))[i];
+          if (j >= nv) {
+            atomicOr(&m->err, kStCorrupt);
+          } else {
+            vin_pos[g * kVmax + i] = (uint16_t)j;
+            vin_bits[g * kVmax + i] = bits;
+            qb[j] = kSentinel;
+          }
+        }
+      }
+    }
+    if (tid == 0) vin_cnt[g] = nverb <= kVmax ? nverb : 0;
+    __syncthreads();
+  }
+
+  // Basis input: every code 0 except the value 1.0 at `pos` (given raw, as verbatim input).
+  __device__ void load_basis(int g, int pos) {
+    const int tid = threadIdx.x;
+    int32_t* qb = q + g * L.nv;
+    for (int j = tid; j < L.nv; j += T) qb[j] = 0;
+    __syncthreads();
+    if (tid == 0) {
+      if (pos >= 0) {
+        qb[pos] = kSentinel;
+        vin_pos[g * kVmax] = (uint16_t)pos;
+        vin_bits[g * kVmax] = RawBits<Real>::to((Real)1.0);
+        vin_cnt[g] = 1;
+      } else {
+        vin_cnt[g] = 0;
+      }
+    }
+    __syncthreads();
+  }
+
+  __device__ Real value_at(int g, int j) const {
+    const int32_t c = q[g * L.nv + j];
+    if (c != kSentinel) return dequant<Real>(c, qp);
+    const int n = vin_cnt[g];
+    for (int i = 0; i < n; ++i)
+      if (vin_pos[g * kVmax + i] == j) return RawBits<Real>::from(vin_bits[g * kVmax + i]);
+    return (Real)0;
+  }
+
+  // Hash slot of a symbol that the histogram inserted; L.hs (and an error flag) when it is
+  // missing, which only a logic error can cause: the probe is bounded either way.
+  __device__ uint32_t find_slot(uint32_t sym) const {
+    uint32_t h = hash_sym(sym) & (uint32_t)(L.hs - 1);
+    for (int probe = 0; probe < L.hs; ++probe) {
+      const uint32_t k = hkey[h];
+      if (k == sym) return h;
+      if (k == kEmpty) break;
+      h = (h + 1) & (uint32_t)(L.hs - 1);
+    }
+    atomicOr(&m->err, kStInternal);
+    return (uint32_t)L.hs;
+  }
+
+  // Quantize one result into slot g position j (Compress(S), first step).
+  __device__ void put_value(int g, int j, Real v) {
+    int32_t c;
+    if (quantize<Real>(v, qp, &c)) {
+      const int i = atomicAdd(&vout_cnt[g], 1);
+      if (i < kVmax) {
+        vout_pos[g * kVmax + i] = (uint16_t)j;
+        vout_bits[g * kVmax + i] = RawBits<Real>::to(v);
+      } else {
+        atomicOr(&m->err, kStVerbatim);
+      }
+      c = 0;
+    }
+    q[g * L.nv + j] = c;
+  }
+
+  // ------------------------------------------------------------------------------------
+  // Compress(S) for one block: q codes + verbatim list -> stream in the output arena.
+  // ------------------------------------------------------------------------------------
+  __device__ void encode(int g, unsigned long long blk, const PassArgs& a);
+};
+
+// Two-queue Huffman lengths over D leaves sorted by (frequency, symbol) in keys (frequency
+// in the upper 16 bits). Leaf first on ties. Writes lens[i] for leaf i; returns max length.
+__device__ inline int huffman_two_queue(const uint32_t* keys, int D, uint32_t* wint,
+                                        uint16_t* parent, uint8_t* lens) {
+  if (D == 1) {
+    lens[0] = 1;
+    return 1;
+  }
+  int lp = 0, ip = 0, nint = 0;
+  for (int mm = 0; mm < D - 1; ++mm) {
+    int pick[2];
+    uint32_t w[2];
+    for (int t = 0; t < 2; ++t) {
+      const uint32_t wl = lp < D ? (keys[lp] >> 16) : 0xFFFFFFFFu;
+      const bool take_leaf = lp < D && (ip >= nint || wl <= wint[ip]);
+      if (take_leaf) {
+        pick[t] = lp;
+        w[t] = wl;
+        lp++;
+      } else {
+        pick[t] = D + ip;
+        w[t] = wint[ip];
+        ip++;
+      }
+    }
+    wint[nint] = w[0] + w[1];
+    parent[pick[0]] = (uint16_t)(D + nint);
+    parent[pick[1]] = (uint16_t)(D + nint);
+    nint++;
+  }
+  // depths top-down (parents have larger indices); lens doubles as depth storage
+  const int total = 2 * D - 1;
+  lens[total - 1] = 0;
+  int lmax = 0;
+  for (int v = total - 2; v >= 0; --v) {
+    const int d = lens[parent[v]] + 1;
+    lens[v] = (uint8_t)d;
+    if (v < D && d > lmax) lmax = d;
+  }
+  return lmax;
+}
+
+template <typename Real>
+__device__ void Worker<Real>::encode(int g, unsigned long long blk, const PassArgs& a) {
+  const int tid = threadIdx.x, nv = L.nv;
+  const int32_t* qb = q + g * nv;
+  const int nverb_raw = vout_cnt[g];
+  const int nverb = nverb_raw < kVmax ? nverb_raw : kVmax;
+  const int C = nv / kChunk;
+  // ---- pass 1: statistics over this thread's values ----
+  const int j0 = tid * vpt;
+  const int32_t q0 = qb[0], q1 = qb[1];
+  int32_t pr = j0 >= 2 ? qb[j0 - 2] : 0, pi = j0 >= 2 ? qb[j0 - 1] : 0;
+  unsigned long long sqh = 0, sql = 0;
+  uint32_t zmax = 0;
+  int nesc = 0;
+  bool cst = true;
+#pragma unroll 4
+  for (int i = 0; i < vpt; ++i) {
+    const int j = j0 + i;
+    const int32_t c = qb[j];
+    const int32_t p = (j & 1) ? pi : pr;
+    const int32_t d = c - p;
+    if (j & 1) pi = c;
+    else pr = c;
+    const uint64_t s2 = (uint64_t)((int64_t)c * (int64_t)c);
+    sqh += s2 >> 32;
+    sql += s2 & 0xffffffffull;
+    const uint32_t z = zigzag(d);
+    zmax = z > zmax ? z : zmax;
+    nesc += (d < -kRadius || d > kRadius) ? 1 : 0;
+    cst = cst && (c == ((j & 1) ? q1 : q0));
+  }
+  const bool is_const = __syncthreads_and(cst) && nverb_raw == 0;
+  const unsigned long long Sh = block_reduce_sum_u64(sqh, m->red);
+  const unsigned long long Sl = block_reduce_sum_u64(sql, m->red);
+  int mode = kModeConst, lmax = 0, width = 0, D = 0;
+  uint32_t pbits = 0, body = 0;
+  uint32_t* keys = (uint32_t*)build;
+  uint32_t* vals = (uint32_t*)(build + 4 * L.p2cap);
+  uint32_t* wint = (uint32_t*)(build + 8 * L.p2cap);
+  uint16_t* parent = (uint16_t*)(build + 8 * L.p2cap + 4 * L.dcap);
+  uint8_t* lens = build + 8 * L.p2cap + 4 * L.dcap + 4 * L.dcap;
+  if (!is_const) {
+    width = bit_width(block_reduce_max<uint32_t>(zmax, m->scan));
+    const uint32_t pack_body = 4u * (((uint32_t)nv * (uint32_t)width + 31u) / 32u);
+    // ---- histogram into the hash table (runs of equal symbols merged first) ----
+    for (int i = tid; i < L.hs; i += T) {
+      hkey[i] = kEmpty;
+      hval[i] = 0;
+    }
+    if (tid == 0) {
+      m->D = 0;
+      m->nesc = 0;
+      m->cnt = 0;
+    }
+    __syncthreads();
+    atomicAdd(&m->nesc, nesc);
+    {
+      int32_t pr2 = j0 >= 2 ? qb[j0 - 2] : 0, pi2 = j0 >= 2 ? qb[j0 - 1] : 0;
+      uint32_t run_sym = 0xFFFFFFFFu, run = 0;
+      for (int i = 0; i <= vpt; ++i) {
+        uint32_t sym = 0xFFFFFFFEu;
+        if (i < vpt) {
+          const int j = j0 + i;
+          const int32_t c = qb[j];
+          const int32_t d = c - ((j & 1) ? pi2 : pr2);
+          if (j & 1) pi2 = c;
+          else pr2 = c;
+          sym = (d < -kRadius || d > kRadius) ? 0u : (uint32_t)(d + 32768);
+        }
+        if (sym == run_sym) {
+          run++;
+          continue;
+        }
+        if (run && *(volatile int*)&m->D <= kHuffMaxD) {
+          uint32_t hslot = hash_sym(run_sym) & (uint32_t)(L.hs - 1);
+          for (int probe = 0; probe < L.hs; ++probe) {
+            const uint32_t k = hkey[hslot];
+            if (k == run_sym) {
+              atomicAdd(&hval[hslot], run);
+              break;
+            }
+            if (k == kEmpty) {
+              const uint32_t old = atomicCAS(&hkey[hslot], kEmpty, run_sym);
+              if (old == kEmpty) {
+                atomicAdd(&m->D, 1);
+                atomicAdd(&hval[hslot], run);
+                break;
+              }
+              if (old == run_sym) {
+                atomicAdd(&hval[hslot], run);
+                break;
+              }
+            }
+            hslot = (hslot + 1) & (uint32_t)(L.hs - 1);
+          }
+        }
+        run_sym = sym;
+        run = 1;
+      }
+    }
+    __syncthreads();
+    D = m->D;
+    const int ne = m->nesc;
+    bool use_huff = false;
+    if (D <= L.dcap && D <= kHuffMaxD) {
+      const int P2 = next_pow2(D);
+      for (int i = tid; i < L.hs; i += T) {
+        if (hkey[i] != kEmpty) {
+          const int k = atomicAdd(&m->cnt, 1);
+          keys[k] = (hval[i] << 16) | hkey[i];
+          vals[k] = (uint32_t)i;
+        }
+      }
+      __syncthreads();
+      for (int i = D + tid; i < P2; i += T) {
+        keys[i] = 0xFFFFFFFFu;
+        vals[i] = 0;
+      }
+      __syncthreads();
+      bitonic_sort(keys, vals, P2);
+      if (tid == 0) m->lmax = huffman_two_queue(keys, D, wint, parent, lens);
+      __syncthreads();
+      lmax = m->lmax;
+      unsigned long long pb = 0;
+      for (int i = tid; i < D; i += T) pb += (unsigned long long)(keys[i] >> 16) * lens[i];
+      pb = block_reduce_sum_u64(pb, m->red) + 32ull * (unsigned long long)ne;
+      pbits = (uint32_t)pb;
+      const uint32_t huff_body = (uint32_t)(pad_to(2 * lmax, 4) + pad_to(2 * D, 4) +
+                                            pad_to(2 * C, 4) + 4 * ((pb + 31) / 32));
+      use_huff = huff_body < pack_body;
+      if (use_huff) {
+        body = huff_body;
+        // canonical order: (length, symbol) ascending
+        for (int i = tid; i < D; i += T) keys[i] = ((uint32_t)lens[i] << 16) | (keys[i] & 0xFFFFu);
+        __syncthreads();
+        bitonic_sort(keys, vals, P2);
+        if (tid == 0) {
+          for (int l = 0; l <= 33; ++l) m->lcount[l] = 0;
+          for (int i = 0; i < D; ++i) m->lcount[keys[i] >> 16]++;
+          int code = 0, idx = 0;
+          for (int l = 1; l <= lmax; ++l) {
+            m->first[l] = code;
+            m->offs[l] = idx;
+            code = (code + m->lcount[l]) << 1;
+            idx += m->lcount[l];
+          }
+        }
+        __syncthreads();
+        for (int i = tid; i < D; i += T) {
+          const int l = (int)(keys[i] >> 16);
+          const uint32_t code = (uint32_t)(m->first[l] + (i - m->offs[l]));
+          hval[vals[i]] = (code << 5) | (uint32_t)l;
+        }
+        __syncthreads();
+      }
+    }
+    if (use_huff) {
+      mode = kModeHuff;
+    } else {
+      mode = kModePack;
+      body = pack_body;
+      pbits = (uint32_t)nv * (uint32_t)width;
+    }
+  }
+  // ---- size and allocation ----
+  const uint32_t body_end = kHdr + body;
+  uint32_t size;
+  if (mode == kModeConst) size = kHdr;
+  else size = (uint32_t)pad_to(pad_to(body_end + 2 * nverb, sizeof(Real)) + sizeof(Real) * nverb, 16);
+  if (tid == 0) {
+    const unsigned long long off = atomicAdd(&a.sc->bump[a.out_id], (unsigned long long)size);
+    m->out_off = off;
+    m->ok = off + size <= a.out_cap;
+    if (!m->ok) {
+      atomicOr(&a.sc->status, kStOverflow);
+      atomicMin(&a.sc->fail_seq, a.seq);
+    }
+  }
+  __syncthreads();
+  const bool ok = m->ok;
+  if (ok) {
+    for (uint32_t i = tid; i < size / 4; i += T) stage[i] = 0;
+    __syncthreads();
+    if (tid == 0) {
+      const int want_dt = sizeof(Real) == 8 ? 2 : 1;
+      const int param = mode == kModeHuff ? lmax : (mode == kModePack ? width : 0);
+      stage[0] = (uint32_t)mode | ((uint32_t)want_dt << 8) | ((uint32_t)b << 16) | ((uint32_t)param << 24);
+      stage[1] = (uint32_t)nverb | ((uint32_t)(mode == kModeHuff ? D : 0) << 16);
+      if (mode == kModeConst) {
+        stage[2] = (uint32_t)q0;
+        stage[3] = (uint32_t)q1;
+      } else {
+        stage[2] = pbits;
+        stage[3] = size;
+      }
+    }
+    if (mode != kModeConst) {
+      uint32_t* pay;
+      if (mode == kModeHuff) {
+        uint16_t* st16 = (uint16_t*)stage;
+        const uint32_t off_sym = kHdr + (uint32_t)pad_to(2 * lmax, 4);
+        const uint32_t off_chunk = off_sym + (uint32_t)pad_to(2 * D, 4);
+        const uint32_t off_pay = off_chunk + (uint32_t)pad_to(2 * C, 4);
+        for (int l = tid + 1; l <= lmax; l += T) st16[kHdr / 2 + l - 1] = (uint16_t)m->lcount[l];
+        for (int i = tid; i < D; i += T) st16[off_sym / 2 + i] = (uint16_t)(keys[i] & 0xFFFFu);
+        // pass 2: bits per thread, then positions
+        uint32_t nb = 0;
+        {
+          int32_t pr2 = j0 >= 2 ? qb[j0 - 2] : 0, pi2 = j0 >= 2 ? qb[j0 - 1] : 0;
+          for (int i = 0; i < vpt; ++i) {
+            const int j = j0 + i;
+            const int32_t c = qb[j];
+            const int32_t d = c - ((j & 1) ? pi2 : pr2);
+            if (j & 1) pi2 = c;
+            else pr2 = c;
+            const uint32_t sym = (d < -kRadius || d > kRadius) ? 0u : (uint32_t)(d + 32768);
+            const uint32_t hs_ = find_slot(sym);
+            nb += (hs_ < (uint32_t)L.hs ? (hval[hs_] & 31u) : 0u) + (sym == 0 ? 32u : 0u);
+          }
+        }
+        uint32_t tot = 0;
+        const uint32_t start = block_excl_scan_u32(nb, m->scan, &tot);
+        // chunk c covers threads [c*64/vpt, (c+1)*64/vpt)
+        // chunk c covers threads [c*tpc, (c+1)*tpc); the thread starts go to the (now free)
+        // internal-weight array
+        const int tpc = kChunk / vpt;
+        uint32_t* tstart = wint;
+        tstart[tid] = start;
+        if (tid == 0) tstart[T] = tot;
+        __syncthreads();
+        for (int c = tid; c < C; c += T) st16[off_chunk / 2 + c] = (uint16_t)(tstart[(c + 1) * tpc] - tstart[c * tpc]);
+        pay = stage + off_pay / 4;
+        BitWriter bw;
+        bw.start(pay, start);
+        {
+          int32_t pr2 = j0 >= 2 ? qb[j0 - 2] : 0, pi2 = j0 >= 2 ? qb[j0 - 1] : 0;
+          for (int i = 0; i < vpt; ++i) {
+            const int j = j0 + i;
+            const int32_t c = qb[j];
+            const int32_t d = c - ((j & 1) ? pi2 : pr2);
+            if (j & 1) pi2 = c;
+            else pr2 = c;
+            const uint32_t sym = (d < -kRadius || d > kRadius) ? 0u : (uint32_t)(d + 32768);
+            const uint32_t hs_ = find_slot(sym);
+            const uint32_t cl = hs_ < (uint32_t)L.hs ? hval[hs_] : 0u;
+            bw.put(cl >> 5, (int)(cl & 31u));
+            if (sym == 0) bw.put((uint32_t)d, 32);
+          }
+        }
+        bw.finish();
+      } else {
+        pay = stage + kHdr / 4;
+        BitWriter bw;
+        bw.start(pay, (uint32_t)(j0 * width));
+        int32_t pr2 = j0 >= 2 ? qb[j0 - 2] : 0, pi2 = j0 >= 2 ? qb[j0 - 1] : 0;
+        for (int i = 0; i < vpt; ++i) {
+          const int j = j0 + i;
+          const int32_t c = qb[j];
+          const int32_t d = c - ((j & 1) ? pi2 : pr2);
+          if (j & 1) pi2 = c;
+          else pr2 = c;
+          bw.put(zigzag(d), width);
+        }
+        bw.finish();
+      }
+      // verbatim section (positions ascending)
+      if (nverb > 0) {
+        __syncthreads();
+        if (tid == 0) {
+          // insertion sort of the (rare) verbatim list by position
+          uint16_t* vp = vout_pos + g * kVmax;
+          uint64_t* vb = vout_bits + g * kVmax;
+          for (int i = 1; i < nverb; ++i) {
+            const uint16_t kp = vp[i];
+            const uint64_t kb = vb[i];
+            int j = i - 1;
+            while (j >= 0 && vp[j] > kp) {
+              vp[j + 1] = vp[j];
+              vb[j + 1] = vb[j];
+              --j;
+            }
+            vp[j + 1] = kp;
+            vb[j + 1] = kb;
+          }
+          uint16_t* st16 = (uint16_t*)stage;
+          for (int i = 0; i < nverb; ++i) st16[body_end / 2 + i] = vp[i];
+          const uint32_t valoff = (uint32_t)pad_to(body_end + 2 * nverb, sizeof(Real));
+          for (int i = 0; i < nverb; ++i) {
+            if (sizeof(Real) == 8) ((uint64_t*)((uint8_t*)stage + valoff))[i] = vb[i];
+            else ((uint32_t*)((uint8_t*)stage + valoff))[i] = (uint32_t)vb[i];
+          }
+        }
+      }
+    }
+    __syncthreads();
+    uint4* dst = (uint4*)(a.out_arena + m->out_off);
+    const uint4* src = (const uint4*)stage;
+    for (uint32_t i = tid; i < size / 16; i += T) dst[i] = src[i];
+    if (tid == 0) {
+      a.out_off[blk] = m->out_off;
+      a.out_len[blk] = size;
+    }
+  }
+  // ---- norm partials and statistics ----
+  if (tid == 0) {
+    // exact sum of q^2: Sh * 2^32 + Sl as a 128-bit value
+    const unsigned long long lo = (Sh << 32) + Sl;
+    const unsigned long long carry0 = (lo < Sl) ? 1ull : 0ull;
+    const unsigned long long hi = (Sh >> 32) + carry0;
+    const unsigned long long old = atomicAdd(&a.sc->acc.sq_lo, lo);
+    const unsigned long long c1 = (old + lo < old) ? 1ull : 0ull;
+    if (hi + c1) atomicAdd(&a.sc->acc.sq_hi, hi + c1);
+    double v = 0.0;
+    const uint64_t* vb = vout_bits + g * kVmax;
+    for (int i = 0; i < nverb; ++i) {
+      const double x = (double)RawBits<Real>::from(vb[i]);
+      v = __dadd_rn(v, __dmul_rn(x, x));
+    }
+    if (a.vsum) a.vsum[blk] = v;
+    if (nverb) atomicAdd(&a.sc->acc.n_verbatim, (unsigned long long)nverb);
+    if (mode != kModeConst) atomicAdd(&a.sc->acc.n_escape, (unsigned long long)m->nesc);
+    atomicAdd(&a.sc->acc.modes[mode], 1ull);
+  }
+  __syncthreads();
+}
+
+}  // namespace sv

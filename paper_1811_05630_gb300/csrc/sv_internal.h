@@ -1,0 +1,49 @@
+// sv_internal.h — launchers shared by the host API and the kernels translation unit.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "sv_block.cuh"
+
+namespace sv {
+
+// Fused gate pass (Algorithm 1 over every slice) for one state; Real by dtype (1 = float).
+cudaError_t launch_pass(const PassArgs& a, int dtype, cudaStream_t st);
+// Pairwise (level by level) sum of n = 2^k per-block verbatim sums into root[0].
+cudaError_t launch_vsum_tree(const double* vsum, unsigned long long n, double* scratch,
+                             double* root, const DevScalars* sc, cudaStream_t st);
+// N, sigma, statistics; resets the accumulators and the bump of arena `reset_id`.
+cudaError_t launch_finalize(DevScalars* sc, const double* root, double two2, int reset_id,
+                            unsigned int seq, cudaStream_t st);
+
+// Standalone codec.
+cudaError_t launch_codec_compress(const void* values, unsigned long long nblocks, int b,
+                                  int dtype, QuantP qp, uint8_t* out, unsigned long long cap,
+                                  unsigned long long* offsets, unsigned int* lengths,
+                                  DevScalars* sc, double* vsum, cudaStream_t st);
+cudaError_t launch_codec_decompress(const uint8_t* in, const unsigned long long* offsets,
+                                    const unsigned int* lengths, unsigned long long nblocks,
+                                    int b, int dtype, QuantP qp, void* values, DevScalars* sc,
+                                    cudaStream_t st);
+// Decoded (reconstructed) amplitudes of blocks [b0, b0 + nb) as FP64 (re, im) into out.
+cudaError_t launch_read_blocks(const uint8_t* arena, const unsigned long long* offs,
+                               const unsigned int* lens, unsigned long long b0,
+                               unsigned long long nb, int b, int dtype, QuantP qp,
+                               double* out, DevScalars* sc, cudaStream_t st);
+
+// Reductions over FP64 (re, im) chunks.
+cudaError_t launch_probs_chunk(const double* amp, unsigned long long start,
+                               unsigned long long count, const int* qubits_dev, int m,
+                               double* bins, cudaStream_t st);
+cudaError_t launch_dot_chunk(const double* a, const double* b, unsigned long long count,
+                             double* acc4, cudaStream_t st);
+
+// Plain (uncompressed) path.
+cudaError_t launch_plain_gate(void* psi, int n, int dtype, const double* G, const int* targets,
+                              int k, unsigned long long cmask, cudaStream_t st);
+cudaError_t launch_plain_basis(void* psi, int n, int dtype, unsigned long long index,
+                               cudaStream_t st);
+cudaError_t launch_plain_read(const void* psi, int dtype, unsigned long long start,
+                              unsigned long long count, double* out, cudaStream_t st);
+
+}  // namespace sv

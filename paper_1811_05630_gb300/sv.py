@@ -1,0 +1,240 @@
+"""Thin ctypes binding of libsv.so (include/sv.h): argument marshalling only.
+
+PyTorch supplies the device memory (one uint8 tensor per pool) and the CUDA streams; every
+step of the simulation runs in the library's CUDA kernels. Importing this module loads
+libsv.so and raises ImportError when it has not been built (``python -m
+paper_1811_05630_gb300.build``) — there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Iterable, Sequence
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsv.so")
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libsv.so is not built; run `python -m paper_1811_05630_gb300.build`")
+_L = ctypes.CDLL(LIB_PATH)
+
+C64, C128 = 1, 2
+OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_NORM, ERR_CORRUPT, ERR_UNSUPPORTED, ERR_TIMEOUT, ERR_INTERNAL = (
+    0, -1, -2, -3, -4, -5, -6, -7, -8)
+_ERR_NAMES = {-1: "SV_ERR_ARG", -2: "SV_ERR_OOM", -3: "SV_ERR_CUDA", -4: "SV_ERR_NORM",
+              -5: "SV_ERR_CORRUPT", -6: "SV_ERR_UNSUPPORTED", -7: "SV_ERR_TIMEOUT", -8: "SV_ERR_INTERNAL"}
+
+
+class SvError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__("%s failed: %s (%d)" % (what, _ERR_NAMES.get(code, "?"), code))
+        self.code = code
+
+
+def _check(rc: int, what: str) -> None:
+    if rc != 0:
+        raise SvError(rc, what)
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [
+        ("pass_index", ctypes.c_uint64), ("compressed_bytes", ctypes.c_uint64),
+        ("table_bytes", ctypes.c_uint64), ("n_blocks", ctypes.c_uint64),
+        ("blocks_const", ctypes.c_uint64), ("blocks_huff", ctypes.c_uint64),
+        ("blocks_pack", ctypes.c_uint64), ("n_verbatim", ctypes.c_uint64),
+        ("n_escape", ctypes.c_uint64), ("norm", ctypes.c_double), ("sigma", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_vp, _i, _d, _sz, _u64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t, ctypes.c_uint64
+_P = ctypes.POINTER
+_SIGS = {
+    "sv_pool_create": ([_vp, _sz, _P(_vp)], _i),
+    "sv_pool_destroy": ([_vp], _i),
+    "sv_pool_usage": ([_vp, _P(_sz), _P(_sz)], _i),
+    "sv_create": ([_vp, _i, _i, _d, _i, _vp, _P(_vp)], _i),
+    "sv_create_ex": ([_vp, _i, _i, _i, _d, _i, _sz, _vp, _P(_vp)], _i),
+    "sv_destroy": ([_vp], _i),
+    "sv_reset_basis": ([_vp, _u64], _i),
+    "sv_apply_gate": ([_vp, _vp, _vp, _i, _vp, _i], _i),
+    "sv_sync": ([_vp], _i),
+    "sv_measure_probs": ([_vp, _vp, _i, _vp], _i),
+    "sv_amplitudes": ([_vp, _vp, _sz, _vp], _i),
+    "sv_read_amplitudes": ([_vp, _u64, _u64, _vp], _i),
+    "sv_fidelity": ([_vp, _vp, _P(_d)], _i),
+    "sv_compressed_bytes": ([_vp, _P(_u64)], _i),
+    "sv_stats": ([_vp, _P(Stats)], _i),
+    "sv_norm": ([_vp, _P(_d)], _i),
+    "sv_block_stream": ([_vp, _u64, _vp, _sz, _P(_sz)], _i),
+    "sv_codec_scratch_bytes": ([], _sz),
+    "sv_codec_compress": ([_vp, _u64, _i, _i, _d, _vp, _u64, _vp, _vp, _vp, _vp, _P(_u64)], _i),
+    "sv_codec_decompress": ([_vp, _vp, _vp, _u64, _i, _i, _d, _vp, _vp, _vp], _i),
+    "sv_version": ([], ctypes.c_char_p),
+}
+for _name, (_args, _res) in _SIGS.items():
+    _f = getattr(_L, _name)
+    _f.argtypes = _args
+    _f.restype = _res
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+def _np_ptr(a: np.ndarray) -> int:
+    return a.ctypes.data
+
+
+class Pool:
+    """One caller-owned device buffer (a torch uint8 tensor) the library sub-allocates."""
+
+    def __init__(self, nbytes: int, device="cuda"):
+        self.buf = torch.empty(int(nbytes), dtype=torch.uint8, device=device)
+        h = ctypes.c_void_p()
+        _check(_L.sv_pool_create(self.buf.data_ptr(), self.buf.numel(), ctypes.byref(h)), "sv_pool_create")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def usage(self):
+        u, c = ctypes.c_size_t(), ctypes.c_size_t()
+        _check(_L.sv_pool_usage(self._h, ctypes.byref(u), ctypes.byref(c)), "sv_pool_usage")
+        return u.value, c.value
+
+    def close(self):
+        if self._h:
+            _check(_L.sv_pool_destroy(self._h), "sv_pool_destroy")
+            self._h = None
+
+
+class State:
+    """A state vector of n qubits kept compressed (error_bound > 0) or plain (0)."""
+
+    def __init__(self, pool: Pool, n: int, slice_log2: int, error_bound: float, dtype: int = C128,
+                 block_log2: int = -1, arena_bytes: int = 0, stream=None):
+        self.pool, self.n, self.dtype, self.eb = pool, n, dtype, error_bound
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        _check(_L.sv_create_ex(pool.handle, n, slice_log2, block_log2, float(error_bound), dtype,
+                               int(arena_bytes), _stream_handle(self.stream), ctypes.byref(h)), "sv_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _check(_L.sv_destroy(self._h), "sv_destroy")
+            self._h = None
+
+    def reset_basis(self, index: int):
+        _check(_L.sv_reset_basis(self._h, int(index)), "sv_reset_basis")
+
+    def apply(self, G, targets: Sequence[int], controls: Sequence[int] = ()):
+        g = np.ascontiguousarray(G, dtype=np.complex128)
+        t = np.ascontiguousarray(targets, dtype=np.int32)
+        c = np.ascontiguousarray(controls if len(controls) else [0], dtype=np.int32)
+        _check(_L.sv_apply_gate(self._h, _np_ptr(g), _np_ptr(t), t.size, _np_ptr(c), len(controls)),
+               "sv_apply_gate")
+
+    def run(self, gates: Iterable) -> "State":
+        for gt in gates:
+            self.apply(gt.matrix, gt.targets, gt.controls)
+        return self
+
+    def sync(self):
+        _check(_L.sv_sync(self._h), "sv_sync")
+
+    def norm(self) -> float:
+        v = ctypes.c_double()
+        _check(_L.sv_norm(self._h, ctypes.byref(v)), "sv_norm")
+        return v.value
+
+    def stats(self) -> dict:
+        st = Stats()
+        _check(_L.sv_stats(self._h, ctypes.byref(st)), "sv_stats")
+        return st.as_dict()
+
+    def compressed_bytes(self) -> int:
+        v = ctypes.c_uint64()
+        _check(_L.sv_compressed_bytes(self._h, ctypes.byref(v)), "sv_compressed_bytes")
+        return v.value
+
+    def probs(self, qubits: Sequence[int]) -> np.ndarray:
+        q = np.ascontiguousarray(qubits, dtype=np.int32)
+        out = np.zeros(1 << q.size, dtype=np.float64)
+        _check(_L.sv_measure_probs(self._h, _np_ptr(q), q.size, _np_ptr(out)), "sv_measure_probs")
+        return out
+
+    def amplitudes(self, idx) -> np.ndarray:
+        ix = np.ascontiguousarray(idx, dtype=np.uint64)
+        out = np.zeros(ix.size, dtype=np.complex128)
+        _check(_L.sv_amplitudes(self._h, _np_ptr(ix), ix.size, _np_ptr(out)), "sv_amplitudes")
+        return out
+
+    def read(self, start: int = 0, count: int | None = None) -> np.ndarray:
+        if count is None:
+            count = (1 << self.n) - start
+        out = np.zeros(count, dtype=np.complex128)
+        _check(_L.sv_read_amplitudes(self._h, start, count, _np_ptr(out)), "sv_read_amplitudes")
+        return out
+
+    def fidelity(self, other: "State") -> float:
+        v = ctypes.c_double()
+        _check(_L.sv_fidelity(self._h, other._h, ctypes.byref(v)), "sv_fidelity")
+        return v.value
+
+    def block_stream(self, b: int) -> bytes:
+        ln = ctypes.c_size_t()
+        _check(_L.sv_block_stream(self._h, b, None, 0, ctypes.byref(ln)), "sv_block_stream")
+        buf = np.zeros(max(ln.value, 1), dtype=np.uint8)
+        _check(_L.sv_block_stream(self._h, b, _np_ptr(buf), buf.size, ctypes.byref(ln)), "sv_block_stream")
+        return buf[: ln.value].tobytes()
+
+
+def codec_scratch_bytes() -> int:
+    return int(_L.sv_codec_scratch_bytes())
+
+
+def codec_compress(values: torch.Tensor, block_log2: int, error_bound: float, cap: int | None = None,
+                   stream=None):
+    """Compress device complex values (complex128/complex64, length a multiple of
+    2^block_log2). Returns (out uint8 tensor, offsets u64 tensor, lengths i32 tensor, used)."""
+    assert values.is_cuda and values.is_contiguous()
+    dtype = C64 if values.dtype == torch.complex64 else C128
+    B = 1 << block_log2
+    nblocks = values.numel() // B
+    assert nblocks * B == values.numel()
+    if cap is None:
+        cap = nblocks * (16 + 4 * 2 * B + 2 * 128 + 8 + 128 * 8 + 32)
+    out = torch.zeros(cap, dtype=torch.uint8, device=values.device)
+    offs = torch.zeros(nblocks, dtype=torch.int64, device=values.device)
+    lens = torch.zeros(nblocks, dtype=torch.int32, device=values.device)
+    scratch = torch.zeros(codec_scratch_bytes(), dtype=torch.uint8, device=values.device)
+    used = ctypes.c_uint64()
+    _check(_L.sv_codec_compress(values.data_ptr(), nblocks, block_log2, dtype, float(error_bound),
+                                out.data_ptr(), cap, offs.data_ptr(), lens.data_ptr(), scratch.data_ptr(),
+                                _stream_handle(stream), ctypes.byref(used)), "sv_codec_compress")
+    return out, offs, lens, used.value
+
+
+def codec_decompress(data: torch.Tensor, offsets: torch.Tensor, lengths: torch.Tensor, block_log2: int,
+                     dtype: int, error_bound: float, stream=None) -> torch.Tensor:
+    nblocks = offsets.numel()
+    tdt = torch.complex64 if dtype == C64 else torch.complex128
+    vals = torch.zeros(nblocks << block_log2, dtype=tdt, device=data.device)
+    scratch = torch.zeros(codec_scratch_bytes(), dtype=torch.uint8, device=data.device)
+    _check(_L.sv_codec_decompress(data.data_ptr(), offsets.data_ptr(), lengths.data_ptr(), nblocks, block_log2,
+                                  dtype, float(error_bound), vals.data_ptr(), scratch.data_ptr(),
+                                  _stream_handle(stream)), "sv_codec_decompress")
+    return vals
+
+
+def version() -> str:
+    return _L.sv_version().decode()

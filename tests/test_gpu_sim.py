@@ -1,0 +1,187 @@
+"""GPU Algorithm 1 (sv_apply_gate through the C ABI) vs the oracle's Algorithm 1.
+
+Every FP step of the pass (dequantize, normalize by sigma, gate, quantize) is an IEEE
+operation in the oracle's order on both sides, so the compressed streams, the stored norm
+and the decoded amplitudes must be identical bit for bit after every checked gate. The plain
+(uncompressed) GPU path is compared with O1 within 1e-12 (FP64) / 1e-5 (FP32) per component.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1811_05630_gb300 import circuits as C
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sv():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_1811_05630_gb300 import sv as m
+
+    return m
+
+
+@pytest.fixture(scope="module")
+def pool(sv):
+    p = sv.Pool(1 << 30)
+    yield p
+
+
+def assert_same_state(st, cs, tag=""):
+    nb = cs.nblocks
+    for b in range(nb):
+        assert st.block_stream(b) == cs.block_stream(b), "%s block %d" % (tag, b)
+    assert st.norm() == cs.norm, tag
+
+
+def run_compare(sv, pool, n, sl, b, dtype, eb, x, gates, every=1, arena_bytes=0):
+    st = sv.State(pool, n, sl, eb, dtype, block_log2=b, arena_bytes=arena_bytes)
+    try:
+        st.reset_basis(x)
+        cs = oracle.CompressedSim(n, sl, b, dtype, eb, x)
+        assert_same_state(st, cs, "init")
+        for i, g in enumerate(gates):
+            st.apply(g.matrix, g.targets, g.controls)
+            cs.apply(g.matrix, g.targets, g.controls)
+            if (i + 1) % every == 0 or i == len(gates) - 1:
+                assert_same_state(st, cs, "gate %d %s" % (i, g.name))
+        got = st.read()
+        ref = cs.read().astype(np.complex128)
+        assert got.tobytes() == ref.tobytes()
+        return st.stats(), got
+    finally:
+        st.close()
+
+
+def test_qft12_config_bit_exact(sv, pool):
+    # 12 qubits, 16 slices of 256 amplitudes, eb = 1e-6, complex128 (one block per slice)
+    n = 12
+    x = C.seeded_index(0, n)
+    stats, got = run_compare(sv, pool, n, 8, 8, oracle.C128, 1e-6, x, C.qft(n))
+    ref = np.exp(2j * np.pi * ((x * np.arange(1 << n)) % (1 << n)) / (1 << n)) / 2 ** (n / 2)
+    F = abs(np.vdot(ref, got)) ** 2 / np.vdot(got, got).real
+    print("QFT12 fidelity vs closed form: 1 - F = %.3e, bytes %d" % (1 - F, stats["compressed_bytes"]))
+    assert 1 - F < 1e-6
+
+
+@pytest.mark.parametrize("dtype", [oracle.C128, oracle.C64])
+def test_qft_cross_block_pairing_bit_exact(sv, pool, dtype):
+    # small blocks (32 amplitudes) so that most targets, SWAP pairs and controls are high
+    n = 12
+    stats, _ = run_compare(sv, pool, n, 7, 5, dtype, 1e-6, C.seeded_index(1, n), C.qft(n), every=7)
+
+
+@pytest.mark.parametrize("dtype", [oracle.C128, oracle.C64])
+@pytest.mark.parametrize("eb", [1e-4, 1e-6])
+def test_random_brickwork_bit_exact(sv, pool, dtype, eb):
+    n = 12
+    run_compare(sv, pool, n, 9, 6, dtype, eb, 0, C.random_brickwork(n, 4, seed=21), every=5)
+
+
+def test_grover_bit_exact_and_success_probability(sv, pool):
+    n, eb = 10, 1e-8
+    marked = C.seeded_index(2, n)
+    k = 3
+    gates = C.grover(n, marked, k)
+    st = sv.State(pool, n, 8, eb, oracle.C128, block_log2=6)
+    try:
+        st.reset_basis(0)
+        st.run(gates)
+        cs = oracle.CompressedSim(n, 8, 6, oracle.C128, eb, 0).run(gates)
+        assert_same_state(st, cs, "grover")
+        p = st.probs(list(range(n)))
+        theta = math.asin(2.0 ** (-n / 2))
+        bound = len(gates) * math.sqrt(2.0 ** (n + 1)) * eb * 1.01
+        assert abs(p[marked] - math.sin((2 * k + 1) * theta) ** 2) <= 2 * bound + bound ** 2
+    finally:
+        st.close()
+
+
+def random_unitary(rng, d):
+    z = rng.standard_normal((d, d)) + 1j * rng.standard_normal((d, d))
+    q, r = np.linalg.qr(z)
+    return q * (np.diag(r) / np.abs(np.diag(r)))
+
+
+@pytest.mark.parametrize("dtype", [oracle.C128, oracle.C64])
+def test_multi_target_controlled_gates_bit_exact(sv, pool, dtype):
+    n, b = 11, 5
+    rng = np.random.default_rng(77)
+    gates = []
+    for _ in range(24):
+        k = int(rng.integers(1, 4))
+        while True:
+            qs = [int(q) for q in rng.permutation(n)]
+            t = qs[:k]
+            if sum(q >= b for q in t) <= 2:
+                break
+        nc = int(rng.integers(0, 3))
+        gates.append(C.Gate(random_unitary(rng, 1 << k), tuple(t), tuple(qs[k:k + nc]), "U%d" % k))
+    run_compare(sv, pool, n, 8, b, dtype, 1e-5, C.seeded_index(9, n), gates, every=4)
+
+
+def test_arena_overflow_is_replayed(sv, pool):
+    # 20 qubits starting from 2 MiB arenas: the random circuit's streams (about 3.5 MB)
+    # outgrow them; sv_sync grows the arena to what the pass asked for and replays, and the
+    # result equals the oracle's
+    n, b = 20, 12
+    gates = C.random_brickwork(n, 2, seed=4)
+    stats, _ = run_compare(sv, pool, n, 14, b, oracle.C128, 1e-7, 0, gates, every=len(gates),
+                           arena_bytes=2 << 20)
+    assert stats["compressed_bytes"] > 2 << 20
+
+
+@pytest.mark.parametrize("dtype,tol", [(oracle.C128, 1e-12), (oracle.C64, 1e-5)])
+def test_plain_path_matches_o1(sv, pool, dtype, tol):
+    n = 12
+    rng = np.random.default_rng(5)
+    gates = C.random_brickwork(n, 3, seed=8) + C.qft(n)
+    for _ in range(6):
+        qs = [int(q) for q in rng.permutation(n)]
+        gates.append(C.Gate(random_unitary(rng, 8), tuple(qs[:3]), (qs[3],), "U3"))
+    st = sv.State(pool, n, n, 0.0, dtype)
+    try:
+        st.run(gates)
+        got = st.read()
+        ref = oracle.PlainSim(n, dtype, 0).run(gates).state.astype(np.complex128)
+        assert np.abs(got.real - ref.real).max() <= tol and np.abs(got.imag - ref.imag).max() <= tol
+        p = st.probs([0, 3, 7])
+        pr = np.zeros(8)
+        idx = np.arange(1 << n)
+        v = ((idx >> 0) & 1) | (((idx >> 3) & 1) << 1) | (((idx >> 7) & 1) << 2)
+        np.add.at(pr, v, np.abs(ref) ** 2)
+        assert np.abs(p - pr / pr.sum()).max() < 10 * tol
+    finally:
+        st.close()
+
+
+def test_fidelity_and_probs_of_compressed_state(sv, pool):
+    n = 12
+    x = C.seeded_index(3, n)
+    gates = C.qft(n)
+    a = sv.State(pool, n, 8, 1e-6, oracle.C128)
+    p = sv.State(pool, n, n, 0.0, oracle.C128)
+    try:
+        a.reset_basis(x)
+        p.reset_basis(x)
+        a.run(gates)
+        p.run(gates)
+        va, vp = a.read(), p.read()
+        F_ref = abs(np.vdot(va, vp)) ** 2 / (np.vdot(va, va).real * np.vdot(vp, vp).real)
+        assert abs(a.fidelity(p) - F_ref) < 1e-12
+        assert 1 - a.fidelity(p) < 1e-6
+        pr = a.probs([0, 1, 11])
+        idx = np.arange(1 << n)
+        v = (idx & 1) | (((idx >> 1) & 1) << 1) | (((idx >> 11) & 1) << 2)
+        ref = np.zeros(8)
+        np.add.at(ref, v, np.abs(va) ** 2)
+        assert np.abs(pr - ref / ref.sum()).max() < 1e-12
+        amps = a.amplitudes([0, 5, 4095])
+        assert np.array_equal(amps, va[[0, 5, 4095]])
+    finally:
+        a.close()
+        p.close()

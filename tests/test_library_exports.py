@@ -1,0 +1,41 @@
+"""The C-ABI library loads and exports every function include/sv.h declares (no GPU
+needed: nothing is called). Also checks the product never touches the oracle."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    txt = open(os.path.join(ROOT, "include", "sv.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\**\s+(sv_[a-z_0-9]+)\s*\(", txt, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ["sv_create", "sv_apply_gate", "sv_measure_probs", "sv_fidelity", "sv_compressed_bytes",
+                 "sv_pool_create", "sv_codec_compress", "sv_codec_decompress"]:
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_1811_05630_gb300 import build
+
+    lib = ctypes.CDLL(build.build())
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_product_does_not_use_the_oracle():
+    pkg = os.path.join(ROOT, "paper_1811_05630_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                src = open(os.path.join(dirpath, f)).read()
+                for bad in ("import oracle", "from oracle", "liboracle", "sv_oracle", "orc_"):
+                    assert bad not in src, (f, bad)
