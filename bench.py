@@ -1,0 +1,365 @@
+"""Benchmark: amplitude-updates/s of the compressed gate pass (Algorithm 1 of Wu et al.,
+PMES 2018) on one GB300, with the plain (uncompressed) GPU path and the CPU oracle beside it.
+
+A step is one gate pass over the whole compressed state: every block is decoded,
+normalized, has the gate applied and is re-encoded (plus the norm finalization). The
+default workload is Grover search on 20 qubits (eb = 1e-8, slice_log2 = 14, complex128):
+the timed steps are consecutive gates of the Grover circuit.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+       [--workload grover20|qft34|qft12|random30]
+Under torchrun each rank runs an independent replica on its own GPU (the method does not
+shard; "replicas only"), rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_1811_05630_gb300 import circuits as C  # noqa: E402
+
+METRIC = "amplitude-updates/s compressed vs plain at fidelity>=1-1e-6; ratio; p99 latency"
+UNIT = "amp-updates/s"
+
+
+def workload(name: str):
+    if name == "grover20":
+        n = 20
+        marked = C.seeded_index(11, n)
+        return dict(name="grover20", n=n, eb=1e-8, slice_log2=14, block_log2=10, dtype=2,
+                    gates=C.grover(n, marked), basis=0, marked=marked,
+                    desc="Grover search, 20 qubits, 804 iterations, complex128, eb 1e-8 abs, slice_log2 14")
+    if name == "qft34":
+        n = 34
+        x = C.seeded_index(0, n)
+        return dict(name="qft34", n=n, eb=1e-7, slice_log2=24, block_log2=12, dtype=2, gates=C.qft(n),
+                    basis=x, desc="QFT on a random basis state, 34 qubits, complex128, eb 1e-7 abs, slice_log2 24")
+    if name == "qft12":
+        n = 12
+        return dict(name="qft12", n=n, eb=1e-6, slice_log2=8, block_log2=8, dtype=2, gates=C.qft(n),
+                    basis=C.seeded_index(0, n), desc="QFT 12 qubits, complex128, eb 1e-6, 16 slices of 256")
+    if name == "random30":
+        n = 30
+        return dict(name="random30", n=n, eb=1e-6, slice_log2=20, block_log2=12, dtype=2,
+                    gates=C.random_brickwork(n, 20, seed=0), basis=0,
+                    desc="random brickwork, 30 qubits, depth 20, complex128, eb 1e-6, slice_log2 20")
+    raise ValueError(name)
+
+
+def start_of_dense_stage(wl):
+    """Timed steps start where the state is no longer mostly empty blocks (QFT: the stage
+    of qubit block_log2 - 1); Grover and random circuits are dense after a few gates."""
+    if wl["name"].startswith("qft"):
+        n, b = wl["n"], wl["block_log2"]
+        return sum(1 + j for j in range(n - 1, b - 1, -1))
+    return wl["n"]
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (SM clock and throttle reasons)."""
+
+    def __init__(self, gpu: int):
+        self.gpu, self.rows, self.proc = gpu, [], None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except FileNotFoundError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for k, nm in enumerate(names):
+                    if r[5 + k].lower().startswith("active"):
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                pass
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {"hbm_gbs": 6800.0, "fallback": True}
+
+
+def grover_fidelity(st, wl, iters):
+    """Fidelity of the GPU state with the exact Grover state a|m> + b sum_{x != m}|x>."""
+    n, m = wl["n"], wl["marked"]
+    th = math.asin(2.0 ** (-n / 2))
+    N = 1 << n
+    a = math.sin((2 * iters + 1) * th)
+    b = math.cos((2 * iters + 1) * th) / math.sqrt(N - 1)
+    v = st.read()
+    ov = a * v[m] + b * (v.sum() - v[m])
+    return abs(ov) ** 2 / np.vdot(v, v).real, abs(v[m]) ** 2 / np.vdot(v, v).real
+
+
+def cpu_oracle_sample(wl, gates, budget_s=15.0):
+    """The oracle's Algorithm 1 (as it stands) on the host: passes of the same circuit on a
+    state of min(n, 20) qubits, until about budget_s of CPU time."""
+    import oracle
+
+    n = min(wl["n"], 20)
+    sel = [g for g in gates if max(g.targets + g.controls) < n]
+    cs = oracle.CompressedSim(n, min(wl["slice_log2"], n), min(wl["block_log2"], n), wl["dtype"], wl["eb"], 0)
+    t0 = time.process_time()
+    w0 = time.time()
+    done = 0
+    for g in sel:
+        cs.apply(g.matrix, g.targets, g.controls)
+        done += 1
+        if time.process_time() - t0 > budget_s:
+            break
+    wall = time.time() - w0
+    return dict(value=(1 << n) * done / wall, unit=UNIT, cores=1, kind="oracle",
+                sample="%d gate passes of the %s circuit on %d qubits (oracle Algorithm 1, one host thread)"
+                       % (done, wl["name"], n))
+
+
+def run_reference(args, rank, world):
+    wl = workload(args.workload)
+    if rank != 0:
+        return None
+    import oracle
+
+    gates = wl["gates"]
+    n = min(wl["n"], 20)
+    sel = [g for g in gates if max(g.targets + g.controls) < n]
+    cs = oracle.CompressedSim(n, min(wl["slice_log2"], n), min(wl["block_log2"], n), wl["dtype"], wl["eb"], 0)
+    per_step = max(1, int(os.environ.get("REF_PASSES_PER_STEP", "4")))
+    it = iter(sel * 1000)
+    for _ in range(args.warmup):
+        for _ in range(per_step):
+            g = next(it)
+            cs.apply(g.matrix, g.targets, g.controls)
+    t = time.time()
+    for _ in range(args.steps):
+        for _ in range(per_step):
+            g = next(it)
+            cs.apply(g.matrix, g.targets, g.controls)
+    dt = time.time() - t
+    val = (1 << n) * per_step * args.steps / dt
+    return {"metric": METRIC, "value": val, "unit": UNIT, "impl": "reference", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if wl["dtype"] == 2 else "f32", "data": "synthetic",
+            "config": {"workload": wl["desc"], "sample": "%d-qubit state, %d passes per step" % (n, per_step)},
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "value": val, "unit": UNIT,
+                             "sample": "oracle Algorithm 1 on %d qubits, %d gate passes per step" % (n, per_step)},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def run_ours(args, rank, world, dist):
+    import torch
+
+    from paper_1811_05630_gb300 import sv
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    wl = workload(args.workload)
+    if args.block_log2:
+        wl["block_log2"] = args.block_log2
+    n = wl["n"]
+    gates = wl["gates"]
+    i0 = start_of_dense_stage(wl)
+    need = args.warmup + args.steps
+    assert i0 + need <= len(gates), "not enough gates for the requested steps"
+    pool_bytes = int(args.pool_gb * (1 << 30))
+    pool = sv.Pool(pool_bytes)
+    st = sv.State(pool, n, wl["slice_log2"], wl["eb"], wl["dtype"], block_log2=wl["block_log2"],
+                  arena_bytes=args.arena_mb << 20)
+    st.reset_basis(wl["basis"])
+    st.run(gates[:i0])
+    for g in gates[i0:i0 + args.warmup]:
+        st.apply(g.matrix, g.targets, g.controls)
+    st.sync()
+    timed = gates[i0 + args.warmup:i0 + need]
+    st.set_pass_timing(True)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev) as clk:
+        e0.record(stream)
+        for g in timed:
+            st.apply(g.matrix, g.targets, g.controls)
+        e1.record(stream)
+        st.sync()
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    kern_ms, npass, alg_bytes = st.pass_timing()
+    stats = st.stats()
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = (1 << n) * len(timed) * world / (ms * 1e-3)
+
+    # end to end through the public API, host buffers: each step copies its gate from
+    # pinned host memory and reads the step's result (the stored norm) back to the host
+    pin = torch.empty(16 * 64, dtype=torch.uint8).pin_memory()
+    e2e_gates = gates[i0 + need:i0 + need + min(args.steps, len(gates) - i0 - need)] or timed
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t = time.time()
+    h2d = d2h = 0
+    for g in e2e_gates:
+        gm = np.ascontiguousarray(g.matrix, dtype=np.complex128)
+        pin_view = pin.numpy()[: gm.nbytes]
+        pin_view[:] = gm.view(np.uint8).reshape(-1)
+        st.apply(pin_view.view(np.complex128).reshape(gm.shape), g.targets, g.controls)
+        h2d += gm.nbytes + 4 * (len(g.targets) + len(g.controls))
+        st.norm()
+        d2h += 8
+    e2e_s = time.time() - t
+    e2e = {"value": (1 << n) * len(e2e_gates) * world / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": h2d // len(e2e_gates), "d2h_bytes_per_step": d2h // len(e2e_gates)}
+
+    result = None
+    if rank == 0:
+        pk = peaks()
+        kern_s = kern_ms * 1e-3
+        achieved = alg_bytes / kern_s / 1e9 if kern_s > 0 else 0.0
+        roof = {"bound": "hbm", "achieved": achieved, "peak": pk.get("hbm_gbs"), "unit": "GB/s",
+                "frac": achieved / pk.get("hbm_gbs", 1.0), "traffic": None,
+                "kernel": "k_pass<double>", "kernel_ms_per_launch": kern_ms / max(npass, 1),
+                "alg_bytes_per_launch": alg_bytes / max(npass, 1),
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "fallback" not in pk else "fallback"}
+        # plain GPU path on the same gates, where it fits
+        plain = None
+        if args.plain:
+            try:
+                st.close()
+                pool.close()
+                del pool
+                torch.cuda.empty_cache()
+                ppool = sv.Pool(((16 if wl["dtype"] == 2 else 8) << n) + (64 << 20))
+                ps = sv.State(ppool, n, n, 0.0, wl["dtype"])
+                ps.reset_basis(wl["basis"])
+                ps.run(gates[:i0 + args.warmup])
+                ps.sync()
+                torch.cuda.synchronize()
+                e0.record(stream)
+                ps.run(timed)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                pms = e0.elapsed_time(e1)
+                plain = (1 << n) * len(timed) / (pms * 1e-3)
+                ps.close()
+                ppool.close()
+            except Exception as ex:  # noqa: BLE001
+                plain = "unavailable: %s" % ex
+        cpu = cpu_oracle_sample(wl, gates, budget_s=args.cpu_budget) if args.cpu_budget > 0 else None
+        fid = None
+        if args.fidelity and wl["name"] == "grover20":
+            fid = full_grover_fidelity(sv, wl)
+        launches_per_pass = 2 + max(1, math.ceil(math.log(max(2, 1 << (n - wl["block_log2"])), 2048)))
+        result = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": len(timed),
+            "warmup": args.warmup, "ms_per_step": ms / len(timed), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if wl["dtype"] == 2 else "f32",
+            "data": "synthetic",
+            "config": {"workload": wl["desc"], "block_log2": wl["block_log2"], "parallelism": "replicas",
+                       "l2": "state streams read and written once per step; no flush (compressed state %d B)"
+                             % stats["compressed_bytes"],
+                       "compressed_bytes": stats["compressed_bytes"],
+                       "compression_ratio": (16 << n) / max(1, stats["compressed_bytes"]),
+                       "plain_amp_updates_per_s": plain,
+                       "ratio_plain_over_compressed": (plain / (value / world)) if isinstance(plain, float) else None,
+                       "fidelity": fid},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
+            "gpu_launches": launches_per_pass * len(timed),
+        }
+    return result
+
+
+def full_grover_fidelity(sv, wl):
+    """Run the whole Grover circuit (outside the timed region) and report its fidelity."""
+    import torch
+
+    pool = sv.Pool(1 << 30)
+    st = sv.State(pool, wl["n"], wl["slice_log2"], wl["eb"], wl["dtype"], block_log2=wl["block_log2"])
+    st.reset_basis(0)
+    st.run(wl["gates"])
+    st.sync()
+    iters = C.grover_iterations(wl["n"])
+    F, p = grover_fidelity(st, wl, iters)
+    st.close()
+    pool.close()
+    torch.cuda.synchronize()
+    return {"fidelity_vs_exact": F, "p_marked": p, "iterations": iters, "passes": len(wl["gates"])}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="grover20", choices=["grover20", "qft34", "qft12", "random30"])
+    ap.add_argument("--block-log2", type=int, default=0)
+    ap.add_argument("--pool-gb", type=float, default=8.0)
+    ap.add_argument("--arena-mb", type=int, default=0)
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-plain", dest="plain", action="store_false")
+    ap.add_argument("--no-fidelity", dest="fidelity", action="store_false")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if args.impl == "reference":
+        res = run_reference(args, rank, world)
+    else:
+        if world > 1:
+            import torch.distributed as dist_mod
+
+            dist_mod.init_process_group("nccl")
+            dist = dist_mod
+        res = run_ours(args, rank, world, dist)
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+    if rank == 0 and res is not None:
+        print(json.dumps(res))
+
+
+if __name__ == "__main__":
+    main()

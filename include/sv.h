@@ -163,6 +163,16 @@ int sv_codec_decompress(const void* in, const uint64_t* offsets, const uint32_t*
                         uint64_t nblocks, int block_log2, int dtype, double error_bound,
                         void* values, void* scratch, void* stream);
 
+/* ---------------------------------------------------------------------------------------
+ * Tracing. sv_set_pass_timing(s, 1) records CUDA events on the state's stream around every
+ * fused pass kernel from then on and zeroes the counters (0 stops recording).
+ * sv_get_pass_timing synchronizes and returns the summed kernel time of the recorded
+ * passes (ms), their number, and their algorithmic bytes: compressed bytes read plus
+ * written, plus 32 bytes of block-table and verbatim-sum traffic per block.
+ * ------------------------------------------------------------------------------------- */
+int sv_set_pass_timing(sv_state* s, int on);
+int sv_get_pass_timing(sv_state* s, double* kernel_ms, uint64_t* passes, uint64_t* bytes);
+
 /* Library version string and the sm architecture it was built for. */
 const char* sv_version(void);
 

@@ -122,6 +122,12 @@ struct sv_state {
   int* qdev = nullptr;
   unsigned long long chunk_amps = 0;
   int sticky_err = 0;
+  // tracing: event pairs around the fused pass kernel
+  bool timing = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_free, ev_pending;
+  double kernel_ms = 0.0;
+  unsigned long long timed_passes = 0;
+  unsigned long long io_base = 0;
 };
 
 namespace {
@@ -244,8 +250,23 @@ int launch_logged(sv_state* s, const Logged& lg) {
     }
   }
   a.ngroups = s->nblocks >> a.h;
+  std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+  if (s->timing && !lg.basis) {
+    if (s->ev_free.empty()) {
+      cudaEventCreate(&ev.first);
+      cudaEventCreate(&ev.second);
+    } else {
+      ev = s->ev_free.back();
+      s->ev_free.pop_back();
+    }
+    cudaEventRecord(ev.first, s->st);
+  }
   cudaError_t e = launch_pass(a, s->dtype == SV_C64 ? 1 : 2, s->st);
   if (e != cudaSuccess) return cuda_err(e);
+  if (ev.first) {
+    cudaEventRecord(ev.second, s->st);
+    s->ev_pending.push_back(ev);
+  }
   e = launch_vsum_tree(s->vsum, s->nblocks, s->tree, s->vroot, s->sc, s->st);
   if (e != cudaSuccess) return cuda_err(e);
   e = launch_finalize(s->sc, s->vroot, s->two2, lg.in_id, lg.seq, s->st);
@@ -436,6 +457,14 @@ int sv_create(sv_pool* pool, int n, int sl, double eb, int dtype, void* stream, 
 int sv_destroy(sv_state* s) {
   if (!s) return SV_ERR_ARG;
   cudaStreamSynchronize(s->st);
+  for (auto& ev : s->ev_free) {
+    cudaEventDestroy(ev.first);
+    cudaEventDestroy(ev.second);
+  }
+  for (auto& ev : s->ev_pending) {
+    cudaEventDestroy(ev.first);
+    cudaEventDestroy(ev.second);
+  }
   region_free(s->pool, &s->psi_r);
   region_free(s->pool, &s->meta_r);
   region_free(s->pool, &s->arena_r[0]);
@@ -492,8 +521,19 @@ int sv_sync(sv_state* s) {
     if (rc) return rc;
     if (h.status == 0) {
       s->log.clear();
+      for (auto& ev : s->ev_pending) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev.first, ev.second);
+        s->kernel_ms += ms;
+        s->timed_passes++;
+        s->ev_free.push_back(ev);
+      }
+      s->ev_pending.clear();
       return SV_OK;
     }
+    // a replay re-records its passes: drop the events of the failed attempt
+    for (auto& ev : s->ev_pending) s->ev_free.push_back(ev);
+    s->ev_pending.clear();
     if (h.status != kStOverflow) return status_to_err(h.status);
     // find the failed pass in the log
     size_t i = 0;
@@ -692,6 +732,33 @@ int sv_fidelity(sv_state* a, sv_state* b, double* out) {
   *out = (h[0] * h[0] + h[1] * h[1]) / (h[2] * h[3]);
   if (!a->plain && (rc = check_status(a))) return rc;
   if (!b->plain && (rc = check_status(b))) return rc;
+  return SV_OK;
+}
+
+int sv_set_pass_timing(sv_state* s, int on) {
+  if (!s || s->plain) return SV_ERR_ARG;
+  int rc = sv_sync(s);
+  if (rc) return rc;
+  DevScalars h;
+  rc = read_scalars(s, &h);
+  if (rc) return rc;
+  s->timing = on != 0;
+  s->kernel_ms = 0.0;
+  s->timed_passes = 0;
+  s->io_base = h.io_bytes;
+  return SV_OK;
+}
+
+int sv_get_pass_timing(sv_state* s, double* kernel_ms, uint64_t* passes, uint64_t* bytes) {
+  if (!s || s->plain) return SV_ERR_ARG;
+  int rc = sv_sync(s);
+  if (rc) return rc;
+  DevScalars h;
+  rc = read_scalars(s, &h);
+  if (rc) return rc;
+  if (kernel_ms) *kernel_ms = s->kernel_ms;
+  if (passes) *passes = s->timed_passes;
+  if (bytes) *bytes = (h.io_bytes - s->io_base) + 32ull * s->nblocks * s->timed_passes;
   return SV_OK;
 }
 

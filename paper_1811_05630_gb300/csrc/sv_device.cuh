@@ -48,6 +48,7 @@ struct DevScalars {
   PassAcc last;                // of the last finalized pass
   unsigned long long last_bytes;
   unsigned long long pass_index;
+  unsigned long long io_bytes;   // compressed bytes read + written, summed over passes
   double sigma;                // scale for the next pass, 1/sqrt(norm)
   double norm;                 // N of the current stored state
   unsigned int status;

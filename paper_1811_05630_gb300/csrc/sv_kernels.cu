@@ -236,6 +236,7 @@ __global__ void k_finalize(DevScalars* sc, const double* root, double two2, int 
   sc->sigma = __ddiv_rn(1.0, __dsqrt_rn(N));
   sc->last = sc->acc;
   sc->last_bytes = sc->bump[reset_id ^ 1];
+  sc->io_bytes += sc->bump[reset_id] + sc->bump[reset_id ^ 1];
   sc->acc.sq_lo = sc->acc.sq_hi = 0;
   sc->acc.n_verbatim = sc->acc.n_escape = 0;
   sc->acc.modes[0] = sc->acc.modes[1] = sc->acc.modes[2] = 0;

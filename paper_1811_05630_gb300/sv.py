@@ -74,6 +74,8 @@ _SIGS = {
     "sv_codec_scratch_bytes": ([], _sz),
     "sv_codec_compress": ([_vp, _u64, _i, _i, _d, _vp, _u64, _vp, _vp, _vp, _vp, _P(_u64)], _i),
     "sv_codec_decompress": ([_vp, _vp, _vp, _u64, _i, _i, _d, _vp, _vp, _vp], _i),
+    "sv_set_pass_timing": ([_vp, _i], _i),
+    "sv_get_pass_timing": ([_vp, _P(_d), _P(_u64), _P(_u64)], _i),
     "sv_version": ([], ctypes.c_char_p),
 }
 for _name, (_args, _res) in _SIGS.items():
@@ -189,6 +191,16 @@ class State:
         v = ctypes.c_double()
         _check(_L.sv_fidelity(self._h, other._h, ctypes.byref(v)), "sv_fidelity")
         return v.value
+
+    def set_pass_timing(self, on: bool = True):
+        _check(_L.sv_set_pass_timing(self._h, 1 if on else 0), "sv_set_pass_timing")
+
+    def pass_timing(self):
+        """(summed fused-kernel ms, passes, algorithmic bytes) since set_pass_timing."""
+        ms, n, by = ctypes.c_double(), ctypes.c_uint64(), ctypes.c_uint64()
+        _check(_L.sv_get_pass_timing(self._h, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(by)),
+               "sv_get_pass_timing")
+        return ms.value, n.value, by.value
 
     def block_stream(self, b: int) -> bytes:
         ln = ctypes.c_size_t()
