@@ -164,6 +164,31 @@ int sv_codec_decompress(const void* in, const uint64_t* offsets, const uint32_t*
                         void* values, void* scratch, void* stream);
 
 /* ---------------------------------------------------------------------------------------
+ * sv_codec_compress_static — sv_codec_compress for callers that cannot allocate device
+ * memory (no scratch argument). The paper has no counterpart: this is a library service.
+ * Who needs it: code that runs where device allocation is forbidden or unavailable, e.g. a
+ * runtime that owns every allocation up front, or a caller without access to an allocator;
+ * such a caller still owns the inputs and outputs (values, out, offsets, lengths) but
+ * cannot provide sv_codec_scratch_bytes() of scratch.
+ * The scratch lives in a fixed array compiled into libsv.so (about 513 KB; every GPU that
+ * loads the library holds it until the process exits): a 256-byte bookkeeping record plus
+ * one double per block. At most SV_STATIC_MAX_BLOCKS blocks per call (SV_ERR_UNSUPPORTED
+ * beyond). Outputs as sv_codec_compress (same streams, same `used`), plus *norm (if not
+ * NULL): the stored norm of the compressed values, N = fl(fl(Sd*(2eb)^2) + V), with Sd the
+ * exact sum of the squared codes and V the pairwise sum of the per-block squares of the
+ * verbatim values (list padded with zeros to a power of two).
+ * The first call on a device looks the array's device address up (once per device, with
+ * that device current); make that first call before any stream capture. Every call clears
+ * the record it uses at its start; the array is shared by all calls on a device and keeps
+ * the last call's contents, so calls that overlap on the GPU (other streams or threads)
+ * race and must be serialized by the caller. Synchronizes `stream`. No memory is allocated.
+ * ------------------------------------------------------------------------------------- */
+#define SV_STATIC_MAX_BLOCKS 65536
+int sv_codec_compress_static(const void* values, uint64_t nblocks, int block_log2, int dtype,
+                             double error_bound, void* out, uint64_t cap, uint64_t* offsets,
+                             uint32_t* lengths, void* stream, uint64_t* used, double* norm);
+
+/* ---------------------------------------------------------------------------------------
  * Tracing. sv_set_pass_timing(s, 1) records CUDA events on the state's stream around every
  * fused pass kernel from then on and zeroes the counters (0 stops recording).
  * sv_get_pass_timing synchronizes and returns the summed kernel time of the recorded

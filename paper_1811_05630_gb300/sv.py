@@ -74,6 +74,7 @@ _SIGS = {
     "sv_codec_scratch_bytes": ([], _sz),
     "sv_codec_compress": ([_vp, _u64, _i, _i, _d, _vp, _u64, _vp, _vp, _vp, _vp, _P(_u64)], _i),
     "sv_codec_decompress": ([_vp, _vp, _vp, _u64, _i, _i, _d, _vp, _vp, _vp], _i),
+    "sv_codec_compress_static": ([_vp, _u64, _i, _i, _d, _vp, _u64, _vp, _vp, _vp, _P(_u64), _P(_d)], _i),
     "sv_set_pass_timing": ([_vp, _i], _i),
     "sv_get_pass_timing": ([_vp, _P(_d), _P(_u64), _P(_u64)], _i),
     "sv_version": ([], ctypes.c_char_p),
@@ -234,6 +235,25 @@ def codec_compress(values: torch.Tensor, block_log2: int, error_bound: float, ca
                                 out.data_ptr(), cap, offs.data_ptr(), lens.data_ptr(), scratch.data_ptr(),
                                 _stream_handle(stream), ctypes.byref(used)), "sv_codec_compress")
     return out, offs, lens, used.value
+
+
+STATIC_MAX_BLOCKS = 65536
+
+
+def codec_compress_static(values: torch.Tensor, block_log2: int, error_bound: float, out: torch.Tensor,
+                          offsets: torch.Tensor, lengths: torch.Tensor, stream=None):
+    """Like codec_compress, for callers that cannot allocate device memory: the caller owns
+    every buffer passed here and the library uses its own fixed scratch array (no scratch
+    argument, nothing allocated). Returns (used bytes, stored norm of the compressed values)."""
+    assert values.is_cuda and values.is_contiguous()
+    dtype = C64 if values.dtype == torch.complex64 else C128
+    nblocks = values.numel() >> block_log2
+    used, norm = ctypes.c_uint64(), ctypes.c_double()
+    _check(_L.sv_codec_compress_static(values.data_ptr(), nblocks, block_log2, dtype, float(error_bound),
+                                       out.data_ptr(), out.numel(), offsets.data_ptr(), lengths.data_ptr(),
+                                       _stream_handle(stream), ctypes.byref(used), ctypes.byref(norm)),
+           "sv_codec_compress_static")
+    return used.value, norm.value
 
 
 def codec_decompress(data: torch.Tensor, offsets: torch.Tensor, lengths: torch.Tensor, block_log2: int,
