@@ -28,8 +28,8 @@ typedef unsigned __int128 u128;
 #define HDR_BYTES 16
 #define SYM_RADIUS 32767   /* |delta| <= 32767 maps to symbol delta + 32768 */
 #define SYM_ESCAPE 0       /* symbol 0: delta follows as 32 raw bits */
-#define CHUNK_SYMS 64      /* symbols per decode chunk */
-#define HUFF_MAX_DISTINCT 1024
+#define CHUNK_SYMS 32      /* symbols per decode chunk */
+#define HUFF_MAX_DISTINCT 256
 #define Q_LIMIT 536870912.0 /* 2^29: |x*r| must be below this to be quantized */
 
 static size_t pad_to(size_t x, size_t a) { return (x + a - 1) / a * a; }

@@ -184,6 +184,7 @@ int launch_logged(sv_state* s, const Logged& lg) {
   a.nv = 2 << s->b;
   a.qp = s->qp;
   a.two2 = s->two2;
+  a.two_r = s->qp.two * s->qp.r;
   a.sc = s->sc;
   a.vsum = s->vsum;
   a.seq = lg.seq;

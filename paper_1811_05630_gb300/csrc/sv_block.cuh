@@ -32,12 +32,26 @@ struct Misc {
   int lcount[34];  // codes per length
 };
 
+// Fixed-point form of one gate pass for complex128 (computed once per CTA): output jj, part
+// p (0 re, 1 im) is W = sum over members m and components c of coef[jj][p][m][c] * q[m][c],
+// with coef = sigma * G * fl(2eb * r) in units of 2^-(F+31), split as hi * 2^31 + lo
+// (lo in [0, 2^31)). Diagonal gates use only m = jj.
+struct FastGate {
+  int F;              // fractional bits of W
+  int diag;           // the gate matrix is diagonal
+  long long margin;   // half-width of the band around a rounding tie sent to the exact path
+  int32_t chi[8][2][8][2], clo[8][2][8][2];
+  int32_t idhi, idlo; // the identity scaled by sigma (members whose controls are not all 1)
+};
+
 // Dynamic shared-memory layout of a worker CTA (host and device agree on it).
 struct Layout {
   int nv, G, hs, dcap, p2cap;
   uint32_t off_q, off_vin_pos, off_vin_bits, off_vout_pos, off_vout_bits, off_hkey, off_hval,
-      off_stage, off_build, off_misc, total;
+      off_stage, off_build, off_misc, off_fast, total;
   uint32_t stage_bytes, build_bytes;
+  uint32_t sort_off, sort_n;  // rank-sort scratch inside the build area
+  uint32_t off_wint, off_parent, off_parent2, off_lens, off_lens2;
 };
 
 __host__ __device__ inline int next_pow2(int x) {
@@ -72,22 +86,34 @@ __host__ __device__ inline Layout make_layout(int b, int G, int csize) {
   L.stage_bytes = (uint32_t)pad_to(kHdr + (size_t)L.nv * 4 + 2 * kVmax + 8 + (size_t)kVmax * csize + 16, 16);
   L.off_stage = o;
   o += L.stage_bytes;
-  // codebook build: keys, vals (p2cap each), internal weights (dcap), parent (2 dcap u16),
-  // lengths (2 dcap u8); decode: LUT (2^kLutBits u32), symbols (dcap u16), chunk starts
-  uint32_t build = (uint32_t)(8 * L.p2cap + 4 * L.dcap + 4 * L.dcap + 2 * L.dcap);
-  uint32_t dec = (uint32_t)(4 * (1 << kLutBits) + 2 * L.dcap + 4 * (L.nv / kChunk + 1));
+  // codebook build: keys, vals (p2cap each), internal weights (dcap), parent and its
+  // ping-pong copy (2 dcap u16 each), depths and copy (2 dcap u8 each), rank-sort scratch
+  // (2 x min(256, dcap) u32). Decode: table (2^kLutBits u32), chunk starts.
+  L.off_wint = (uint32_t)(8 * L.p2cap);
+  // the internal-weight array doubles as the table of 257 thread start bits (pass 2)
+  L.off_parent = L.off_wint + (uint32_t)(4 * (L.dcap > 257 ? L.dcap : 257));
+  L.off_parent2 = L.off_parent + (uint32_t)(4 * L.dcap);
+  L.off_lens = L.off_parent2 + (uint32_t)(4 * L.dcap);
+  L.off_lens2 = L.off_lens + (uint32_t)pad_to(2 * L.dcap, 4);
+  L.sort_off = L.off_lens2 + (uint32_t)pad_to(2 * L.dcap, 4);
+  L.sort_n = L.dcap < 256 ? L.dcap : 256;
+  uint32_t build = L.sort_off + (uint32_t)(8 * L.sort_n);
+  uint32_t dec = (uint32_t)(4 * (1 << kLutBits) + 4 * (L.nv / kChunk + 1));
   L.build_bytes = (uint32_t)pad_to(build > dec ? build : dec, 16);
   L.off_build = o;
   o += L.build_bytes;
   L.off_misc = o;
   o += (uint32_t)pad_to(sizeof(Misc), 16);  // scalars and scan workspace
+  L.off_fast = o;
+  o += (uint32_t)pad_to(sizeof(FastGate), 16);
   L.total = o;
   return L;
 }
 
+// One thread per 32-value decode chunk (every thread decodes one chunk), 32 to 256 threads.
 __host__ __device__ inline int worker_threads(int b) {
   int nv = 2 << b;
-  int t = nv / 2;
+  int t = nv / kChunk;
   if (t > 256) t = 256;
   if (t < 32) t = 32;
   return t;
@@ -108,6 +134,7 @@ struct PassArgs {
   float gf[2 * 64];
   QuantP qp;
   double two2;
+  double two_r;       // fl(2eb * r), the dequantize-requantize factor (about 1)
   unsigned long long ngroups;
   const uint8_t* in_arena;
   const unsigned long long* in_off;
@@ -157,23 +184,31 @@ struct Worker {
 
   // ------------------------------------------------------------------------------------
   // Decompress(S) for one block: stream -> q codes (verbatim slots hold kSentinel and
-  // their raw values go to the vin list). Returns nothing; errors set m->err.
+  // their raw values go to the vin list). The stream is first copied into the stage buffer
+  // with 16-byte loads; every later read is from shared memory. Errors set m->err.
   // ------------------------------------------------------------------------------------
   __device__ void decode(int g, const uint8_t* s, uint32_t len) {
     const int tid = threadIdx.x, nv = L.nv;
     int32_t* qb = q + g * nv;
+    const bool fits = len >= kHdr && len <= L.stage_bytes && (len & 15) == 0;
+    if (fits) {
+      const uint4* src = (const uint4*)s;
+      uint4* dst = (uint4*)stage;
+      for (uint32_t i = tid; i < len / 16; i += T) dst[i] = __ldg(src + i);
+    }
+    __syncthreads();
+    const uint8_t* sm = (const uint8_t*)stage;
     uint32_t h0 = 0, h1 = 0, h2 = 0, h3 = 0;
-    if (len >= kHdr) {
-      const uint4 hv = __ldg((const uint4*)s);
-      h0 = hv.x;
-      h1 = hv.y;
-      h2 = hv.z;
-      h3 = hv.w;
+    if (fits) {
+      h0 = stage[0];
+      h1 = stage[1];
+      h2 = stage[2];
+      h3 = stage[3];
     }
     const int mode = h0 & 0xff, dt = (h0 >> 8) & 0xff, bl = (h0 >> 16) & 0xff, param = h0 >> 24;
     const int nverb = h1 & 0xffff, D = h1 >> 16;
     const int want_dt = sizeof(Real) == 8 ? 2 : 1;
-    bool bad = len < kHdr || dt != want_dt || bl != b || mode > kModePack;
+    bool bad = !fits || dt != want_dt || bl != b || mode > kModePack;
     uint32_t body_end = kHdr;
     if (!bad && mode == kModeConst) {
       if (nverb != 0) bad = true;
@@ -193,11 +228,16 @@ struct Worker {
       body_end = kHdr + 4 * nwords;
       if (body_end > total) bad = true;
       if (!bad) {
-        const uint32_t* w = (const uint32_t*)(s + kHdr);
+        const uint32_t* w = (const uint32_t*)(sm + kHdr);
         for (int i = 0; i < vpt; ++i) {
           const int j = tid * vpt + i;
           uint32_t z = 0;
-          if (width) z = peek32(w, (uint64_t)j * width, nwords) >> (32 - width);
+          if (width) {
+            const uint32_t pos = (uint32_t)j * (uint32_t)width, wi = pos >> 5, sh = pos & 31;
+            const uint32_t a0 = w[wi], a1 = wi + 1 < nwords ? w[wi + 1] : 0u;
+            const uint32_t pk = sh ? (a0 << sh) | (a1 >> (32 - sh)) : a0;
+            z = pk >> (32 - width);
+          }
           qb[j] = unzigzag(z);
         }
       }
@@ -211,12 +251,12 @@ struct Worker {
       body_end = off_pay + 4 * nwords;
       if (lmax < 1 || lmax > 24 || D < 1 || D > L.dcap || body_end > total) bad = true;
       uint32_t* lut = (uint32_t*)build;
-      uint16_t* symtab = (uint16_t*)(build + 4 * (1 << kLutBits));
-      uint32_t* cstart = (uint32_t*)(build + 4 * (1 << kLutBits) + pad_to(2 * L.dcap, 4));
+      uint32_t* cstart = (uint32_t*)(build + 4 * (1 << kLutBits));
+      const uint16_t* symtab = (const uint16_t*)(sm + off_sym);
       if (!bad) {
         if (tid == 0) {
           int code = 0, idx = 0;
-          const uint16_t* cnt = (const uint16_t*)(s + kHdr);
+          const uint16_t* cnt = (const uint16_t*)(sm + kHdr);
           for (int l = 1; l <= lmax; ++l) {
             const int c = cnt[l - 1];
             m->first[l] = code;
@@ -227,11 +267,10 @@ struct Worker {
           }
           if (idx != D) atomicOr(&m->err, kStCorrupt);
         }
-        for (int i = tid; i < D; i += T) symtab[i] = ((const uint16_t*)(s + off_sym))[i];
         for (int i = tid; i < (1 << kLutBits); i += T) lut[i] = 0;
       }
       uint32_t cb = 0;
-      if (!bad && tid < C) cb = ((const uint16_t*)(s + off_chunk))[tid];
+      if (!bad && tid < C) cb = ((const uint16_t*)(sm + off_chunk))[tid];
       uint32_t ctot = 0;
       const uint32_t cs = block_excl_scan_u32(cb, m->scan, &ctot);  // syncs
       if (!bad && ctot != pbits) bad = true;
@@ -251,44 +290,8 @@ struct Worker {
         }
       }
       __syncthreads();
-      if (!bad && tid < C && !m->err) {
-        const uint32_t* w = (const uint32_t*)(s + off_pay);
-        uint64_t pos = cstart[tid];
-        const uint64_t end = cstart[tid + 1];
-        bool cerr = false;
-        for (int i = 0; i < kChunk; ++i) {
-          const uint32_t pk = peek32(w, pos, nwords);
-          const uint32_t e = lut[pk >> (32 - kLutBits)];
-          int idx = -1, l = 0;
-          if (e) {
-            idx = (int)(e >> 8) - 1;
-            l = (int)(e & 0xff);
-          } else {
-            for (l = kLutBits + 1; l <= lmax; ++l) {
-              const int c = (int)(pk >> (32 - l));
-              if (m->lcount[l] && c >= m->first[l] && c - m->first[l] < m->lcount[l]) {
-                idx = m->offs[l] + c - m->first[l];
-                break;
-              }
-            }
-          }
-          if (idx < 0 || idx >= D) {
-            cerr = true;
-            break;
-          }
-          pos += (uint64_t)l;
-          const int sym = symtab[idx];
-          int32_t d;
-          if (sym == 0) {
-            d = (int32_t)peek32(w, pos, nwords);
-            pos += 32;
-          } else {
-            d = sym - 32768;
-          }
-          qb[tid * kChunk + i] = d;
-        }
-        if (cerr || pos != end) atomicOr(&m->err, kStCorrupt);
-      }
+      if (!bad && tid < C && !m->err) decode_chunk(qb + tid * kChunk, (const uint32_t*)(sm + off_pay), nwords,
+                                                   cstart[tid], cstart[tid + 1], lut, symtab, D, lmax);
     }
     if (bad && tid == 0) atomicOr(&m->err, kStCorrupt);
     __syncthreads();
@@ -314,33 +317,98 @@ struct Worker {
           qb[tid * vpt + i] = off.x;
         }
       }
-    __syncthreads();
     // verbatim section: ascending positions, then raw values (aligned to the value size)
     if (nverb > kVmax) {
       if (tid == 0) atomicOr(&m->err, kStVerbatim);
     } else if (nverb > 0 && !bad) {
-      const uint32_t posoff = body_end;
-      const uint32_t valoff = (uint32_t)pad_to(posoff + 2 * nverb, sizeof(Real));
-      if (valoff + sizeof(Real) * nverb > total) {
-        if (tid == 0) atomicOr(&m->err, kStCorrupt);
-      } else {
-        for (int i = tid; i < nverb; i += T) {
-          const int j = ((const uint16_t*)(s + posoff))[i];
-          uint64_t bits;
-          if (sizeof(Real) == 8) bits = ((const uint64_t*)(s + valoff))[i];
-          else bits = ((const uint32_t*)(s + valoff))[i];
-          if (j >= nv) {
-            atomicOr(&m->err, kStCorrupt);
-          } else {
-            vin_pos[g * kVmax + i] = (uint16_t)j;
-            vin_bits[g * kVmax + i] = bits;
-            qb[j] = kSentinel;
-          }
-        }
-      }
+      __syncthreads();
+      read_verbatim(g, sm, body_end, total, nverb);
     }
     if (tid == 0) vin_cnt[g] = nverb <= kVmax ? nverb : 0;
     __syncthreads();
+  }
+
+  __device__ __forceinline__ void read_verbatim(int g, const uint8_t* sm, uint32_t posoff, uint32_t total,
+                                             int nverb) {
+    const uint32_t valoff = (uint32_t)pad_to(posoff + 2 * nverb, sizeof(Real));
+    if (valoff + sizeof(Real) * nverb > total) {
+      if (threadIdx.x == 0) atomicOr(&m->err, kStCorrupt);
+      return;
+    }
+    for (int i = threadIdx.x; i < nverb; i += T) {
+      const int j = ((const uint16_t*)(sm + posoff))[i];
+      uint64_t bits;
+      if (sizeof(Real) == 8) bits = ((const uint64_t*)(sm + valoff))[i];
+      else bits = ((const uint32_t*)(sm + valoff))[i];
+      if (j >= L.nv) {
+        atomicOr(&m->err, kStCorrupt);
+      } else {
+        vin_pos[g * kVmax + i] = (uint16_t)j;
+        vin_bits[g * kVmax + i] = bits;
+        q[g * L.nv + j] = kSentinel;
+      }
+    }
+  }
+
+  // One 32-symbol chunk of a Huffman payload (shared-memory words), through a 64-bit bit
+  // buffer that holds at least 32 unread bits before every symbol.
+  __device__ __forceinline__ void decode_chunk(int32_t* out, const uint32_t* w, uint32_t nwords,
+                                               uint32_t pos, uint32_t end, const uint32_t* lut,
+                                               const uint16_t* symtab, int D, int lmax) {
+    uint32_t wi = pos >> 5;
+    const int sh = (int)(pos & 31);
+    const uint64_t w0 = wi < nwords ? w[wi] : 0u, w1 = wi + 1 < nwords ? w[wi + 1] : 0u;
+    uint64_t buf = ((w0 << 32) | w1) << sh;
+    int nbuf = 64 - sh;
+    wi += 2;
+    bool cerr = false;
+#pragma unroll 4
+    for (int i = 0; i < kChunk; ++i) {
+      if (nbuf < 32) {
+        buf |= (uint64_t)(wi < nwords ? w[wi] : 0u) << (32 - nbuf);
+        ++wi;
+        nbuf += 32;
+      }
+      const uint32_t pk = (uint32_t)(buf >> 32);
+      const uint32_t e = lut[pk >> (32 - kLutBits)];
+      int idx = -1, l = 0;
+      if (e) {
+        idx = (int)(e >> 8) - 1;
+        l = (int)(e & 0xff);
+      } else {
+        for (l = kLutBits + 1; l <= lmax; ++l) {
+          const int c = (int)(pk >> (32 - l));
+          if (m->lcount[l] && c >= m->first[l] && c - m->first[l] < m->lcount[l]) {
+            idx = m->offs[l] + c - m->first[l];
+            break;
+          }
+        }
+      }
+      if (idx < 0 || idx >= D) {
+        cerr = true;
+        break;
+      }
+      buf <<= l;
+      nbuf -= l;
+      pos += (uint32_t)l;
+      const int sym = symtab[idx];
+      int32_t d;
+      if (sym == 0) {
+        if (nbuf < 32) {
+          buf |= (uint64_t)(wi < nwords ? w[wi] : 0u) << (32 - nbuf);
+          ++wi;
+          nbuf += 32;
+        }
+        d = (int32_t)(uint32_t)(buf >> 32);
+        buf <<= 32;
+        nbuf -= 32;
+        pos += 32;
+      } else {
+        d = sym - 32768;
+      }
+      out[i] = d;
+    }
+    if (cerr || pos != end) atomicOr(&m->err, kStCorrupt);
   }
 
   // Basis input: every code 0 except the value 1.0 at `pos` (given raw, as verbatim input).
@@ -407,46 +475,94 @@ struct Worker {
   __device__ void encode(int g, unsigned long long blk, const PassArgs& a);
 };
 
-// Two-queue Huffman lengths over D leaves sorted by (frequency, symbol) in keys (frequency
-// in the upper 16 bits). Leaf first on ties. Writes lens[i] for leaf i; returns max length.
-__device__ inline int huffman_two_queue(const uint32_t* keys, int D, uint32_t* wint,
-                                        uint16_t* parent, uint8_t* lens) {
-  if (D == 1) {
-    lens[0] = 1;
-    return 1;
-  }
+// Two-queue Huffman merge over D >= 2 leaves sorted by (frequency, symbol) in keys (frequency
+// in the upper 16 bits): each step joins the two lightest queue heads, the leaf queue first on
+// equal weight. Writes parent[v] for every node but the root (node D-1+... = 2D-2). The queue
+// heads are kept in registers so that a step waits on at most the refill of what it consumed.
+__device__ inline void huffman_merge(const uint32_t* keys, int D, uint32_t* wint, uint16_t* parent) {
+  constexpr uint32_t INF = 0xFFFFFFFFu;
   int lp = 0, ip = 0, nint = 0;
+  uint32_t cl = keys[0] >> 16;
+  uint32_t cl_next = keys[1] >> 16;
+  uint32_t ci = INF;
   for (int mm = 0; mm < D - 1; ++mm) {
     int pick[2];
     uint32_t w[2];
+#pragma unroll
     for (int t = 0; t < 2; ++t) {
-      const uint32_t wl = lp < D ? (keys[lp] >> 16) : 0xFFFFFFFFu;
-      const bool take_leaf = lp < D && (ip >= nint || wl <= wint[ip]);
-      if (take_leaf) {
+      if (cl <= ci) {
         pick[t] = lp;
-        w[t] = wl;
-        lp++;
+        w[t] = cl;
+        ++lp;
+        cl = cl_next;
+        cl_next = lp + 1 < D ? (keys[lp + 1] >> 16) : INF;
       } else {
         pick[t] = D + ip;
-        w[t] = wint[ip];
-        ip++;
+        w[t] = ci;
+        ++ip;
+        ci = ip < nint ? wint[ip] : INF;
       }
     }
-    wint[nint] = w[0] + w[1];
+    const uint32_t wn = w[0] + w[1];
+    wint[nint] = wn;
     parent[pick[0]] = (uint16_t)(D + nint);
     parent[pick[1]] = (uint16_t)(D + nint);
-    nint++;
+    if (ip == nint) ci = wn;  // the new node is the only one in its queue
+    ++nint;
   }
-  // depths top-down (parents have larger indices); lens doubles as depth storage
-  const int total = 2 * D - 1;
-  lens[total - 1] = 0;
-  int lmax = 0;
-  for (int v = total - 2; v >= 0; --v) {
-    const int d = lens[parent[v]] + 1;
-    lens[v] = (uint8_t)d;
-    if (v < D && d > lmax) lmax = d;
+}
+
+// Depth of every node of the merged tree by pointer jumping (all threads): d[v] += d[p[v]],
+// p[v] = p[p[v]], ping-ponging between two copies. Depths are at most 18 for the <= 8192
+// symbols of a block, so 6 rounds (jumps of 64) reach the root from every node and leave the
+// result in (parent, depth).
+__device__ inline void tree_depths(int D, uint16_t* parent, uint8_t* depth, uint16_t* parent2,
+                                   uint8_t* depth2) {
+  const int total = 2 * D - 1, root = total - 1;
+  for (int v = threadIdx.x; v < total; v += blockDim.x) {
+    depth[v] = v == root ? 0 : 1;
+    if (v == root) parent[v] = (uint16_t)root;
   }
-  return lmax;
+  __syncthreads();
+  uint16_t *pa = parent, *pb = parent2;
+  uint8_t *da = depth, *db = depth2;
+  for (int round = 0; round < 6; ++round) {
+    for (int v = threadIdx.x; v < total; v += blockDim.x) {
+      const int p = pa[v];
+      db[v] = (uint8_t)(da[v] + da[p]);
+      pb[v] = pa[p];
+    }
+    __syncthreads();
+    uint16_t* tp = pa;
+    pa = pb;
+    pb = tp;
+    uint8_t* td = da;
+    da = db;
+    db = td;
+  }
+}
+
+// Sort n (key, val) pairs ascending by key (keys distinct). Up to 256: every element finds
+// its rank in one pass (scratch tk/tv); larger lists: bitonic over the padded power p2.
+__device__ inline void sort_pairs(uint32_t* key, uint32_t* val, int n, int p2, uint32_t* tk,
+                                  uint32_t* tv) {
+  if (n <= 256) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const uint32_t k = key[i];
+      int r = 0;
+      for (int j = 0; j < n; ++j) r += key[j] < k;
+      tk[r] = k;
+      tv[r] = val[i];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      key[i] = tk[i];
+      val[i] = tv[i];
+    }
+    __syncthreads();
+  } else {
+    bitonic_sort(key, val, p2);
+  }
 }
 
 template <typename Real>
@@ -487,9 +603,13 @@ __device__ void Worker<Real>::encode(int g, unsigned long long blk, const PassAr
   uint32_t pbits = 0, body = 0;
   uint32_t* keys = (uint32_t*)build;
   uint32_t* vals = (uint32_t*)(build + 4 * L.p2cap);
-  uint32_t* wint = (uint32_t*)(build + 8 * L.p2cap);
-  uint16_t* parent = (uint16_t*)(build + 8 * L.p2cap + 4 * L.dcap);
-  uint8_t* lens = build + 8 * L.p2cap + 4 * L.dcap + 4 * L.dcap;
+  uint32_t* wint = (uint32_t*)(build + L.off_wint);
+  uint16_t* parent = (uint16_t*)(build + L.off_parent);
+  uint16_t* parent2 = (uint16_t*)(build + L.off_parent2);
+  uint8_t* lens = build + L.off_lens;
+  uint8_t* lens2 = build + L.off_lens2;
+  uint32_t* tsk = (uint32_t*)(build + L.sort_off);  // rank-sort scratch
+  uint32_t* tsv = tsk + L.sort_n;
   if (!is_const) {
     width = bit_width(block_reduce_max<uint32_t>(zmax, m->scan));
     const uint32_t pack_body = 4u * (((uint32_t)nv * (uint32_t)width + 31u) / 32u);
@@ -568,8 +688,17 @@ __device__ void Worker<Real>::encode(int g, unsigned long long blk, const PassAr
         vals[i] = 0;
       }
       __syncthreads();
-      bitonic_sort(keys, vals, P2);
-      if (tid == 0) m->lmax = huffman_two_queue(keys, D, wint, parent, lens);
+      sort_pairs(keys, vals, D, P2, tsk, tsv);
+      if (D == 1) {
+        if (tid == 0) lens[0] = 1;
+      } else {
+        if (tid == 0) huffman_merge(keys, D, wint, parent);
+        __syncthreads();
+        tree_depths(D, parent, lens, parent2, lens2);
+      }
+      if (tid == 0) m->lmax = 0;
+      __syncthreads();
+      for (int i = tid; i < D; i += T) atomicMax(&m->lmax, (int)lens[i]);
       __syncthreads();
       lmax = m->lmax;
       unsigned long long pb = 0;
@@ -582,12 +711,12 @@ __device__ void Worker<Real>::encode(int g, unsigned long long blk, const PassAr
       if (use_huff) {
         body = huff_body;
         // canonical order: (length, symbol) ascending
+        if (tid < 34) m->lcount[tid] = 0;
         for (int i = tid; i < D; i += T) keys[i] = ((uint32_t)lens[i] << 16) | (keys[i] & 0xFFFFu);
         __syncthreads();
-        bitonic_sort(keys, vals, P2);
+        for (int i = tid; i < D; i += T) atomicAdd(&m->lcount[lens[i]], 1);
+        sort_pairs(keys, vals, D, P2, tsk, tsv);
         if (tid == 0) {
-          for (int l = 0; l <= 33; ++l) m->lcount[l] = 0;
-          for (int i = 0; i < D; ++i) m->lcount[keys[i] >> 16]++;
           int code = 0, idx = 0;
           for (int l = 1; l <= lmax; ++l) {
             m->first[l] = code;

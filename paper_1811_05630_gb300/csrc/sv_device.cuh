@@ -23,10 +23,10 @@ namespace sv {
 // ---- format constants -----------------------------------------------------------------
 constexpr int kHdr = 16;
 constexpr int kRadius = 32767;
-constexpr int kChunk = 64;            // symbols per decode chunk
-constexpr int kHuffMaxD = 1024;       // more distinct symbols: PACK
-constexpr int kHashSlots = 2048;      // >= 2 * kHuffMaxD
-constexpr int kLutBits = 11;          // decode table width
+constexpr int kChunk = 32;            // symbols per decode chunk
+constexpr int kHuffMaxD = 256;        // more distinct symbols: PACK
+constexpr int kHashSlots = 512;       // >= 2 * kHuffMaxD
+constexpr int kLutBits = 10;          // decode table width
 constexpr int kVmax = 128;            // GPU limit: verbatim values per block
 constexpr int kModeConst = 0, kModeHuff = 1, kModePack = 2;
 constexpr int32_t kSentinel = INT32_MIN;  // q slot of a verbatim value
@@ -213,7 +213,7 @@ __device__ __forceinline__ unsigned long long block_reduce_sum_u64(unsigned long
 }
 
 // Bitonic sort of n (power of two) (key, val) pairs in shared memory, ascending by key.
-__device__ inline void bitonic_sort(uint32_t* key, uint32_t* val, int n) {
+inline __device__ __noinline__ void bitonic_sort(uint32_t* key, uint32_t* val, int n) {
   for (int k = 2; k <= n; k <<= 1) {
     for (int j = k >> 1; j > 0; j >>= 1) {
       for (int i = threadIdx.x; i < n; i += blockDim.x) {

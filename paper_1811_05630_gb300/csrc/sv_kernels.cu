@@ -37,10 +37,165 @@ __device__ __forceinline__ unsigned long long insert_zero_bit(unsigned long long
 }
 
 // ---------------------------------------------------------------------------------------
+// complex128 fast path. The exact step chain of a pass (x' = fl(q 2eb), y = fl(sigma x'),
+// z = ordered sum of fl products, t = fl(z r), q' = rint(t)) lands within 2^-48 R Q of the
+// real number T = sum c q with c = sigma G (2eb r) (R: largest row sum of |c|, Q = 2^29 the
+// code limit). W below is T in fixed point with error at most 3 2^-F. Where W is farther
+// than the sum of both bounds (plus 2^-21 for the verbatim test) from a rounding tie and
+// inside the code range, rint(t) = round(W) and the value is not verbatim; otherwise that
+// component is recomputed with the exact step chain. Results are identical either way.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ int ceil_log2(double x) {
+  const int e = ilogb(x);  // 2^e <= x < 2^(e+1)
+  return scalbn(1.0, e) == x ? e : e + 1;
+}
+
+__device__ void fast_prepare(FastGate* fg, const PassArgs& a, double sigma) {
+  const double s1 = __dmul_rn(a.use_sigma ? sigma : 1.0, a.two_r);
+  const int K = a.K;
+  double R = fabs(s1);
+  if (a.apply_gate) {
+    for (int jj = 0; jj < K; ++jj) {
+      double row = 0.0;
+      for (int m = 0; m < K; ++m)
+        row += fabs(__dmul_rn(a.g[2 * (jj * K + m)], s1)) + fabs(__dmul_rn(a.g[2 * (jj * K + m) + 1], s1));
+      R = row > R ? row : R;
+    }
+  }
+  const int cl = R > 0.0 ? ceil_log2(R) : 0;
+  int F = 30 - (cl > 0 ? cl : 0);
+  if (!(R > 0.0) || cl > 16 || !isfinite(R)) F = -1;  // fast path off
+  fg->F = F;
+  if (F < 0) return;
+  fg->margin = (long long)ceil(R * scalbn(1.0, F - 19)) + 3 + (1ll << (F > 21 ? F - 21 : 0));
+  const double scale = scalbn(1.0, F + 31);
+  auto fix = [&](double c, int32_t* hi, int32_t* lo) {
+    const long long v = __double2ll_rn(__dmul_rn(c, scale));
+    *hi = (int32_t)(v >> 31);
+    *lo = (int32_t)(v & 0x7fffffffll);
+  };
+  fix(s1, &fg->idhi, &fg->idlo);
+  if (!a.apply_gate) return;
+  int diag = 1;
+  for (int jj = 0; jj < K; ++jj)
+    for (int m = 0; m < K; ++m) {
+      const double A = __dmul_rn(a.g[2 * (jj * K + m)], s1);
+      const double Bc = __dmul_rn(a.g[2 * (jj * K + m) + 1], s1);
+      if (m != jj && (A != 0.0 || Bc != 0.0)) diag = 0;
+      // re += A q_re - B q_im ; im += B q_re + A q_im
+      fix(A, &fg->chi[jj][0][m][0], &fg->clo[jj][0][m][0]);
+      fix(-Bc, &fg->chi[jj][0][m][1], &fg->clo[jj][0][m][1]);
+      fix(Bc, &fg->chi[jj][1][m][0], &fg->clo[jj][1][m][0]);
+      fix(A, &fg->chi[jj][1][m][1], &fg->clo[jj][1][m][1]);
+    }
+  fg->diag = diag;
+}
+
+// round(W / 2^F) when it provably equals the exact chain's code; false otherwise
+__device__ __forceinline__ bool fast_round(long long W, int F, long long margin, int32_t* q) {
+  const long long half = 1ll << (F - 1);
+  const long long qn = (W + half) >> F;
+  const long long frac = W - (qn << F);
+  if (frac < margin - half || frac >= half - margin) return false;
+  if (qn >= (1ll << 29) - 1 || qn <= -((1ll << 29) - 1)) return false;
+  *q = (int32_t)qn;
+  return true;
+}
+
+// the exact step chain for one output component of a tuple (no verbatim input)
+__device__ __forceinline__ double exact_component(const PassArgs& a, double sigma, const int32_t* qv,
+                                                  int jj, int p, bool ctrl) {
+  if (!ctrl) {
+    const double x = __dmul_rn((double)qv[2 * jj + p], a.qp.two);
+    return a.use_sigma ? __dmul_rn(sigma, x) : x;
+  }
+  double ar = 0.0, ai = 0.0;
+  for (int m = 0; m < a.K; ++m) {
+    double yr = __dmul_rn((double)qv[2 * m], a.qp.two), yi = __dmul_rn((double)qv[2 * m + 1], a.qp.two);
+    if (a.use_sigma) {
+      yr = __dmul_rn(sigma, yr);
+      yi = __dmul_rn(sigma, yi);
+    }
+    const double gr = a.g[2 * (jj * a.K + m)], gi = a.g[2 * (jj * a.K + m) + 1];
+    const double pr = __dsub_rn(__dmul_rn(gr, yr), __dmul_rn(gi, yi));
+    const double pi = __dadd_rn(__dmul_rn(gr, yi), __dmul_rn(gi, yr));
+    if (m == 0) {
+      ar = pr;
+      ai = pi;
+    } else {
+      ar = __dadd_rn(ar, pr);
+      ai = __dadd_rn(ai, pi);
+    }
+  }
+  return p ? ai : ar;
+}
+
+// One tuple through the exact step chain in the value type (verbatim inputs; complex64).
+template <typename Real, int KM>
+__device__ __forceinline__ void tuple_exact(Worker<Real>& w, const PassArgs& a, Real sg, int bp, bool ctrl) {
+  using A = Arith<Real>;
+  const Layout& L = w.L;
+  Real yr[KM], yi[KM];
+  int gs[KM], js[KM];
+#pragma unroll
+  for (int mm = 0; mm < KM; ++mm) {
+    if (mm < a.K) {
+      const int p = bp + a.pos_delta[mm];
+      const int g = p / L.nv;
+      const int j = p - g * L.nv;
+      gs[mm] = g;
+      js[mm] = j;
+      const Real xr = w.value_at(g, j), xi = w.value_at(g, j + 1);
+      yr[mm] = a.use_sigma ? A::mul(sg, xr) : xr;
+      yi[mm] = a.use_sigma ? A::mul(sg, xi) : xi;
+    }
+  }
+  if (ctrl) {
+    Real zr[KM], zi[KM];
+#pragma unroll
+    for (int jj = 0; jj < KM; ++jj) {
+      if (jj < a.K) {
+        Real ar = 0, ai = 0;
+#pragma unroll
+        for (int mm = 0; mm < KM; ++mm) {
+          if (mm < a.K) {
+            const Real gr = gate_coef<Real>(a, 2 * (jj * a.K + mm));
+            const Real gi = gate_coef<Real>(a, 2 * (jj * a.K + mm) + 1);
+            const Real pr = A::sub(A::mul(gr, yr[mm]), A::mul(gi, yi[mm]));
+            const Real pi = A::add(A::mul(gr, yi[mm]), A::mul(gi, yr[mm]));
+            if (mm == 0) {
+              ar = pr;
+              ai = pi;
+            } else {
+              ar = A::add(ar, pr);
+              ai = A::add(ai, pi);
+            }
+          }
+        }
+        zr[jj] = ar;
+        zi[jj] = ai;
+      }
+    }
+#pragma unroll
+    for (int mm = 0; mm < KM; ++mm)
+      if (mm < a.K) {
+        yr[mm] = zr[mm];
+        yi[mm] = zi[mm];
+      }
+  }
+#pragma unroll
+  for (int mm = 0; mm < KM; ++mm)
+    if (mm < a.K) {
+      w.put_value(gs[mm], js[mm], yr[mm]);
+      w.put_value(gs[mm], js[mm] + 1, yi[mm]);
+    }
+}
+
+// ---------------------------------------------------------------------------------------
 // Algorithm 1: for the gate G, for every slice: Decompress, Normalize, GateComputation,
 // Compress. One CTA per group of 2^h coupled blocks (grid-stride over the groups).
 // ---------------------------------------------------------------------------------------
-template <typename Real>
+template <typename Real, int KM>
 __global__ void __launch_bounds__(256) k_pass(const PassArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   using A = Arith<Real>;
@@ -58,6 +213,9 @@ __global__ void __launch_bounds__(256) k_pass(const PassArgs a) {
   const double sigma = a.use_sigma ? *(volatile double*)&a.sc->sigma : 1.0;
   const Real sg = (Real)sigma;  // complex64: sigma rounded to float once
   const int B = L.nv / 2;
+  FastGate* fg = (FastGate*)(smem + L.off_fast);
+  constexpr bool kFast = sizeof(Real) == 8;
+  if (kFast && threadIdx.x == 0) fast_prepare(fg, a, sigma);  // visible after the loop's barrier
   for (unsigned long long grp = blockIdx.x; grp < a.ngroups; grp += gridDim.x) {
     unsigned long long base = grp;
     for (int l = 0; l < a.h; ++l) base = insert_zero_bit(base, a.high_pos[l]);
@@ -87,60 +245,77 @@ __global__ void __launch_bounds__(256) k_pass(const PassArgs a) {
       const unsigned long long gidx = (blks[0] << a.b) | o;
       const bool ctrl = a.apply_gate && ((gidx & a.cmask) == a.cmask);
       const int bp = 2 * (int)o;
-      Real yr[8], yi[8];
-      int gs[8], js[8];
+      if (kFast && fg->F >= 0) {
+        int32_t qv[2 * KM];
+        int gq[KM], jq[KM];
+        bool sentinel = false;
 #pragma unroll
-      for (int mm = 0; mm < 8; ++mm) {
-        if (mm < a.K) {
-          const int p = bp + a.pos_delta[mm];
-          const int g = p / L.nv;
-          const int j = p - g * L.nv;
-          gs[mm] = g;
-          js[mm] = j;
-          const Real xr = w.value_at(g, j), xi = w.value_at(g, j + 1);
-          yr[mm] = a.use_sigma ? A::mul(sg, xr) : xr;
-          yi[mm] = a.use_sigma ? A::mul(sg, xi) : xi;
-        }
-      }
-      if (ctrl) {
-        Real zr[8], zi[8];
+        for (int mm = 0; mm < KM; ++mm)
+          if (mm < a.K) {
+            const int p = bp + a.pos_delta[mm];
+            gq[mm] = p / L.nv;
+            jq[mm] = p - gq[mm] * L.nv;
+            qv[2 * mm] = w.q[p];
+            qv[2 * mm + 1] = w.q[p + 1];
+            sentinel |= qv[2 * mm] == kSentinel || qv[2 * mm + 1] == kSentinel;
+          }
+        if (!sentinel) {
+          const int F = fg->F;
+          const long long margin = fg->margin;
+          int32_t out[2 * KM];
+          unsigned int exact_mask = 0;
 #pragma unroll
-        for (int jj = 0; jj < 8; ++jj) {
-          if (jj < a.K) {
-            Real ar = 0, ai = 0;
+          for (int jj = 0; jj < KM; ++jj)
+            if (jj < a.K) {
 #pragma unroll
-            for (int mm = 0; mm < 8; ++mm) {
-              if (mm < a.K) {
-                const Real gr = gate_coef<Real>(a, 2 * (jj * a.K + mm));
-                const Real gi = gate_coef<Real>(a, 2 * (jj * a.K + mm) + 1);
-                const Real pr = A::sub(A::mul(gr, yr[mm]), A::mul(gi, yi[mm]));
-                const Real pi = A::add(A::mul(gr, yi[mm]), A::mul(gi, yr[mm]));
-                if (mm == 0) {
-                  ar = pr;
-                  ai = pi;
+              for (int p = 0; p < 2; ++p) {
+                long long sh = 0, sl = 0;
+                if (ctrl && fg->diag) {
+#pragma unroll
+                  for (int c = 0; c < 2; ++c) {
+                    const long long qq = qv[2 * jj + c];
+                    sh += qq * fg->chi[jj][p][jj][c];
+                    sl += (qq * fg->clo[jj][p][jj][c]) >> 4;
+                  }
+                } else if (ctrl) {
+#pragma unroll
+                  for (int m = 0; m < KM; ++m)
+                    if (m < a.K) {
+#pragma unroll
+                      for (int c = 0; c < 2; ++c) {
+                        const long long qq = qv[2 * m + c];
+                        sh += qq * fg->chi[jj][p][m][c];
+                        sl += (qq * fg->clo[jj][p][m][c]) >> 4;
+                      }
+                    }
                 } else {
-                  ar = A::add(ar, pr);
-                  ai = A::add(ai, pi);
+                  const long long qq = qv[2 * jj + p];
+                  sh = qq * fg->idhi;
+                  sl = (qq * fg->idlo) >> 4;
                 }
+                if (!fast_round(sh + (sl >> 27), F, margin, &out[2 * jj + p])) exact_mask |= 1u << (2 * jj + p);
               }
             }
-            zr[jj] = ar;
-            zi[jj] = ai;
-          }
-        }
+          double zx[2 * KM];
+          if (exact_mask) {
 #pragma unroll
-        for (int mm = 0; mm < 8; ++mm)
-          if (mm < a.K) {
-            yr[mm] = zr[mm];
-            yi[mm] = zi[mm];
+            for (int e = 0; e < 2 * KM; ++e)
+              if ((exact_mask >> e) & 1u) zx[e] = exact_component(a, sigma, qv, e >> 1, e & 1, ctrl);
           }
+#pragma unroll
+          for (int mm = 0; mm < KM; ++mm)
+            if (mm < a.K) {
+#pragma unroll
+              for (int p = 0; p < 2; ++p) {
+                const int e = 2 * mm + p;
+                if ((exact_mask >> e) & 1u) w.put_value(gq[mm], jq[mm] + p, (Real)zx[e]);
+                else w.q[gq[mm] * L.nv + jq[mm] + p] = out[e];
+              }
+            }
+          continue;
+        }
       }
-#pragma unroll
-      for (int mm = 0; mm < 8; ++mm)
-        if (mm < a.K) {
-          w.put_value(gs[mm], js[mm], yr[mm]);
-          w.put_value(gs[mm], js[mm] + 1, yi[mm]);
-        }
+      tuple_exact<Real, KM>(w, a, sg, bp, ctrl);
     }
     __syncthreads();
     // ---- Compress(S) ----
@@ -152,21 +327,28 @@ __global__ void __launch_bounds__(256) k_pass(const PassArgs a) {
   }
 }
 
-template <typename Real>
-static cudaError_t launch_pass_t(const PassArgs& a, cudaStream_t st) {
+template <typename Real, int KM>
+static cudaError_t launch_pass_k(const PassArgs& a, cudaStream_t st) {
   const Layout L = make_layout(a.b, a.G, (int)sizeof(Real));
-  static int configured = 0;
-  if (configured < (int)L.total) {
-    cudaError_t e = cudaFuncSetAttribute(k_pass<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_pass<Real, KM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     if (e != cudaSuccess) return e;
-    configured = 227 * 1024;
+    configured = true;
   }
   if (L.total > 227 * 1024) return cudaErrorInvalidValue;
   const int T = worker_threads(a.b);
   unsigned long long grid = a.ngroups;
   if (grid > 0x7fffffffull) grid = 0x7fffffffull;
-  k_pass<Real><<<(unsigned int)grid, T, L.total, st>>>(a);
+  k_pass<Real, KM><<<(unsigned int)grid, T, L.total, st>>>(a);
   return cudaGetLastError();
+}
+
+template <typename Real>
+static cudaError_t launch_pass_t(const PassArgs& a, cudaStream_t st) {
+  if (a.K <= 2) return launch_pass_k<Real, 2>(a, st);
+  if (a.K <= 4) return launch_pass_k<Real, 4>(a, st);
+  return launch_pass_k<Real, 8>(a, st);
 }
 
 cudaError_t launch_pass(const PassArgs& a, int dtype, cudaStream_t st) {

@@ -15,7 +15,7 @@ import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libsv.so")
+LIB_PATH = os.environ.get("SV_LIBRARY") or os.path.join(_HERE, "libsv.so")
 if not os.path.exists(LIB_PATH):
     raise ImportError("libsv.so is not built; run `python -m paper_1811_05630_gb300.build`")
 _L = ctypes.CDLL(LIB_PATH)

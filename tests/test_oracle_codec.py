@@ -80,12 +80,13 @@ def test_modes_selected_by_rule():
     rng = np.random.default_rng(0)
     s, info = oracle.compress_block(gen_block("const", 8, rng, oracle.C128), 8, oracle.C128, 1e-6)
     assert info["mode"] == oracle.MODE_CONST
-    # peaked (Gaussian) deltas: Huffman beats fixed width
+    # peaked (Gaussian) deltas with few distinct symbols: Huffman beats fixed width
     v = gen_block("normal", 12, rng, oracle.C128)
-    s, info = oracle.compress_block(v, 12, oracle.C128, 1e-5)
-    assert info["mode"] == oracle.MODE_HUFF and info["n_distinct"] <= 1024
+    s, info = oracle.compress_block(v, 12, oracle.C128, 1e-4)
+    assert info["mode"] == oracle.MODE_HUFF and info["n_distinct"] <= 256
+    # more than 256 distinct symbols: PACK
     s, info = oracle.compress_block(gen_block("wide", 12, rng, oracle.C128), 12, oracle.C128, 1e-6)
-    assert info["n_distinct"] > 1024 and info["mode"] == oracle.MODE_PACK
+    assert info["n_distinct"] > 256 and info["mode"] == oracle.MODE_PACK
 
 
 def test_escapes_roundtrip():
@@ -166,7 +167,7 @@ def parse_stream(s, b, dtype):
         off += (2 * param + 3) // 4 * 4
         syms = struct.unpack_from("<%dH" % D, s, off)
         off += (2 * D + 3) // 4 * 4
-        C = (2 << b) // 64
+        C = (2 << b) // 32
         chunks = struct.unpack_from("<%dH" % C, s, off)
         assert sum(chunks) == pbits
         out.update(counts=counts, syms=syms, pbits=pbits)
