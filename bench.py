@@ -159,10 +159,10 @@ def run_reference(args, rank, world):
     import oracle
 
     gates = wl["gates"]
-    n = min(wl["n"], 20)
+    n = min(wl["n"], 14)  # bounded sample: the same circuit's passes on a 14-qubit state
     sel = [g for g in gates if max(g.targets + g.controls) < n]
     cs = oracle.CompressedSim(n, min(wl["slice_log2"], n), min(wl["block_log2"], n), wl["dtype"], wl["eb"], 0)
-    per_step = max(1, int(os.environ.get("REF_PASSES_PER_STEP", "4")))
+    per_step = 1
     it = iter(sel * 1000)
     for _ in range(args.warmup):
         for _ in range(per_step):
@@ -328,6 +328,87 @@ def full_grover_fidelity(sv, wl):
     return {"fidelity_vs_exact": F, "p_marked": p, "iterations": iters, "passes": len(wl["gates"])}
 
 
+def run_full_circuit(args):
+    """Whole-circuit run (QFT34 is the target configuration): every pass, compressed bytes
+    after every gate, exact fidelity against the closed form, marginal probabilities, and
+    the plain GPU path timed on the same dense-stage gates where its vector fits."""
+    import torch
+
+    from paper_1811_05630_gb300 import sv
+
+    wl = workload(args.workload)
+    if args.block_log2:
+        wl["block_log2"] = args.block_log2
+    n, gates = wl["n"], wl["gates"]
+    pool = sv.Pool(int(args.pool_gb * (1 << 30)))
+    st = sv.State(pool, n, wl["slice_log2"], wl["eb"], wl["dtype"], block_log2=wl["block_log2"],
+                  arena_bytes=args.arena_mb << 20)
+    st.reset_basis(wl["basis"])
+    st.sync()
+    raw = (16 if wl["dtype"] == 2 else 8) << n
+    per_gate = []
+    stream = torch.cuda.current_stream()
+    t_all = time.time()
+    kern_total = 0.0
+    st.set_pass_timing(True)
+    with ClockSampler(0) as clk:
+        for i, g in enumerate(gates):
+            st.apply(g.matrix, g.targets, g.controls)
+            stt = st.stats()  # synchronizes: per-gate compressed size
+            per_gate.append(stt["compressed_bytes"])
+    wall = time.time() - t_all
+    kern_ms, npass, alg_bytes = st.pass_timing()
+    x = wl["basis"]
+    fid = st.fidelity_qft(x) if wl["name"].startswith("qft") else None
+    m = min(10, n)
+    p = st.probs(list(range(m)))
+    pool_used, pool_cap = pool.usage()
+    rng = np.random.default_rng(1)
+    idx = rng.integers(0, 1 << n, size=2000, dtype=np.uint64)
+    amps = st.amplitudes(idx)
+    norm = st.norm()
+    samp = np.abs(amps) ** 2 / norm * (1 << n)
+    res = {
+        "workload": wl["desc"], "block_log2": wl["block_log2"], "gates": len(gates),
+        "amp_updates_per_s_wall": (1 << n) * len(gates) / wall,
+        "amp_updates_per_s_kernel": (1 << n) * npass / (kern_ms * 1e-3) if kern_ms else None,
+        "kernel_ms_total": kern_ms, "wall_s": wall, "fused_kernel_gbs": alg_bytes / (kern_ms * 1e-3) / 1e9,
+        "fidelity_vs_closed_form": fid,
+        "compression_ratio_final": raw / per_gate[-1], "compression_ratio_min": raw / max(per_gate),
+        "compressed_bytes_max": max(per_gate), "compressed_bytes_final": per_gate[-1],
+        "marginal_probs_max_abs_dev_from_uniform": float(np.abs(p - 2.0 ** -m).max()),
+        "sampled_prob_ratio_mean": float(samp.mean()), "sampled_prob_ratio_std": float(samp.std()),
+        "pool_used_bytes": pool_used, "clocks": clk.summary(),
+        "bytes_per_gate": per_gate,
+    }
+    st.close()
+    pool.close()
+    del st, pool
+    import gc
+
+    gc.collect()
+    torch.cuda.empty_cache()
+    if args.plain:
+        try:
+            i0 = start_of_dense_stage(wl)
+            sel = gates[i0:i0 + args.steps]
+            ppool = sv.Pool(raw + (64 << 20))
+            ps = sv.State(ppool, n, n, 0.0, wl["dtype"])
+            ps.reset_basis(x)
+            ps.sync()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ps.run(sel)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            res["plain_amp_updates_per_s_dense_stage"] = (1 << n) * len(sel) / (e0.elapsed_time(e1) * 1e-3)
+            ps.close()
+            ppool.close()
+        except Exception as ex:  # noqa: BLE001
+            res["plain_amp_updates_per_s_dense_stage"] = "unavailable: %s" % ex
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -341,7 +422,12 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-plain", dest="plain", action="store_false")
     ap.add_argument("--no-fidelity", dest="fidelity", action="store_false")
+    ap.add_argument("--full-circuit", action="store_true",
+                    help="run the whole circuit once (per-gate sizes, closed-form fidelity)")
     args = ap.parse_args()
+    if args.full_circuit:
+        print(json.dumps(run_full_circuit(args)))
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     dist = None

@@ -139,6 +139,13 @@ int sv_compressed_bytes(sv_state* s, uint64_t* out);
 int sv_stats(sv_state* s, sv_stats_t* out);
 int sv_norm(sv_state* s, double* out);
 
+/* Overlap with the exact QFT of the basis state |x> (the closed form
+ * 2^{-n/2} sum_y exp(2 pi i (x y mod 2^n) / 2^n) |y>, which the plain simulator reaches):
+ * out[0], out[1] = re, im of <ref|psi>, out[2] = <psi|psi> (psi the stored amplitudes), so
+ * the fidelity is (out[0]^2 + out[1]^2) / out[2]. Streams the state in decoded chunks; a
+ * validation service for states too large for a plain reference. Synchronizing. */
+int sv_overlap_qft(sv_state* s, uint64_t x, double* out);
+
 /* Copy block `b`'s stream (current state) to host `out` (capacity `cap` bytes); *len gets
  * its length. SV_ERR_ARG when cap is too small. Used to compare streams byte by byte. */
 int sv_block_stream(sv_state* s, uint64_t b, uint8_t* out, size_t cap, size_t* len);

@@ -763,6 +763,31 @@ int sv_get_pass_timing(sv_state* s, double* kernel_ms, uint64_t* passes, uint64_
   return SV_OK;
 }
 
+int sv_overlap_qft(sv_state* s, uint64_t x, double* out) {
+  if (!s || !out || (x >> s->n) || s->n < 1) return SV_ERR_ARG;
+  int rc = sv_sync(s);
+  if (rc) return rc;
+  rc = ensure_aux(s);
+  if (rc) return rc;
+  cudaMemsetAsync(s->acc, 0, 4 * sizeof(double), s->st);
+  const unsigned long long dim = 1ull << s->n;
+  for (unsigned long long st = 0; st < dim; st += s->chunk_amps) {
+    rc = read_chunk(s, st, s->chunk_amps, s->chunk[0]);
+    if (rc) return rc;
+    cudaError_t e = launch_qft_overlap_chunk(s->chunk[0], st, s->chunk_amps, x, s->n, s->acc, s->st);
+    if (e != cudaSuccess) return cuda_err(e);
+  }
+  double h[4];
+  cudaError_t e = cudaMemcpyAsync(h, s->acc, sizeof(h), cudaMemcpyDeviceToHost, s->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+  if (e != cudaSuccess) return cuda_err(e);
+  const double scale = 1.0 / std::sqrt(std::ldexp(1.0, s->n));  // 2^{-n/2}
+  out[0] = h[0] * scale;
+  out[1] = h[1] * scale;
+  out[2] = h[2];
+  return s->plain ? SV_OK : check_status(s);
+}
+
 size_t sv_codec_scratch_bytes(void) { return round_up(sizeof(DevScalars), 256); }
 
 int sv_codec_compress(const void* values, uint64_t nblocks, int bl, int dtype, double eb, void* out,

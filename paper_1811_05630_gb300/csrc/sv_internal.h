@@ -38,6 +38,9 @@ cudaError_t launch_probs_chunk(const double* amp, unsigned long long start,
 cudaError_t launch_dot_chunk(const double* a, const double* b, unsigned long long count,
                              double* acc4, cudaStream_t st);
 
+cudaError_t launch_qft_overlap_chunk(const double* amp, unsigned long long start, unsigned long long count,
+                                     unsigned long long x, int n, double* acc, cudaStream_t st);
+
 // Plain (uncompressed) path.
 cudaError_t launch_plain_gate(void* psi, int n, int dtype, const double* G, const int* targets,
                               int k, unsigned long long cmask, cudaStream_t st);

@@ -649,6 +649,40 @@ cudaError_t launch_dot_chunk(const double* a, const double* b, unsigned long lon
   return cudaGetLastError();
 }
 
+// Overlap with the QFT of a basis state, 2^{-n/2} exp(2 pi i (x y mod 2^n) / 2^n) (the
+// closed form the exact simulator reaches): acc[0..1] += conj(ref) . psi, acc[2] += |psi|^2.
+__global__ void k_qft_overlap_chunk(const double* amp, unsigned long long start, unsigned long long count,
+                                    unsigned long long x, int n, double* acc) {
+  double s[3] = {0, 0, 0};
+  const unsigned long long mask = n >= 64 ? ~0ull : ((1ull << n) - 1ull);
+  const double inv_half = 1.0 / (double)(1ull << (n - 1));  // exact power of two
+  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < count;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    const unsigned long long y = start + i;
+    const unsigned long long t = (x * y) & mask;  // x y mod 2^n (the low n bits of the product)
+    double sn, cs;
+    sincospi((double)t * inv_half, &sn, &cs);
+    const double pr = amp[2 * i], pi = amp[2 * i + 1];
+    s[0] += cs * pr + sn * pi;
+    s[1] += cs * pi - sn * pr;
+    s[2] += pr * pr + pi * pi;
+  }
+  for (int k = 0; k < 3; ++k) {
+    double v = s[k];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&acc[k], v);
+  }
+}
+
+cudaError_t launch_qft_overlap_chunk(const double* amp, unsigned long long start, unsigned long long count,
+                                     unsigned long long x, int n, double* acc, cudaStream_t st) {
+  unsigned long long blocks = (count + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  if (blocks == 0) blocks = 1;
+  k_qft_overlap_chunk<<<(unsigned int)blocks, 256, 0, st>>>(amp, start, count, x, n, acc);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------------------
 // Plain path: the full amplitude vector updated in place (the comparison baseline).
 // ---------------------------------------------------------------------------------------

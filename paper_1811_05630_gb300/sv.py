@@ -75,6 +75,7 @@ _SIGS = {
     "sv_codec_compress": ([_vp, _u64, _i, _i, _d, _vp, _u64, _vp, _vp, _vp, _vp, _P(_u64)], _i),
     "sv_codec_decompress": ([_vp, _vp, _vp, _u64, _i, _i, _d, _vp, _vp, _vp], _i),
     "sv_codec_compress_static": ([_vp, _u64, _i, _i, _d, _vp, _u64, _vp, _vp, _vp, _P(_u64), _P(_d)], _i),
+    "sv_overlap_qft": ([_vp, _u64, _vp], _i),
     "sv_set_pass_timing": ([_vp, _i], _i),
     "sv_get_pass_timing": ([_vp, _P(_d), _P(_u64), _P(_u64)], _i),
     "sv_version": ([], ctypes.c_char_p),
@@ -192,6 +193,12 @@ class State:
         v = ctypes.c_double()
         _check(_L.sv_fidelity(self._h, other._h, ctypes.byref(v)), "sv_fidelity")
         return v.value
+
+    def fidelity_qft(self, x: int) -> float:
+        """Fidelity with the exact QFT of |x> (closed form), computed on the GPU."""
+        out = np.zeros(3, dtype=np.float64)
+        _check(_L.sv_overlap_qft(self._h, int(x), _np_ptr(out)), "sv_overlap_qft")
+        return float((out[0] ** 2 + out[1] ** 2) / out[2])
 
     def set_pass_timing(self, on: bool = True):
         _check(_L.sv_set_pass_timing(self._h, 1 if on else 0), "sv_set_pass_timing")

@@ -68,6 +68,22 @@ def test_qft12_config_bit_exact(sv, pool):
     assert 1 - F < 1e-6
 
 
+def test_qft_overlap_matches_host(sv, pool):
+    # sv_overlap_qft streams the state against the closed form on the GPU
+    n = 14
+    x = C.seeded_index(5, n)
+    st = sv.State(pool, n, 10, 1e-6, oracle.C128, block_log2=8)
+    try:
+        st.reset_basis(x)
+        st.run(C.qft(n))
+        got = st.read()
+        ref = np.exp(2j * np.pi * ((x * np.arange(1 << n)) % (1 << n)) / (1 << n)) / 2 ** (n / 2)
+        F = abs(np.vdot(ref, got)) ** 2 / np.vdot(got, got).real
+        assert abs(st.fidelity_qft(x) - F) < 1e-12
+    finally:
+        st.close()
+
+
 @pytest.mark.parametrize("dtype", [oracle.C128, oracle.C64])
 def test_qft_cross_block_pairing_bit_exact(sv, pool, dtype):
     # small blocks (32 amplitudes) so that most targets, SWAP pairs and controls are high
