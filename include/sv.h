@@ -114,6 +114,31 @@ int sv_reset_basis(sv_state* s, uint64_t index);
 int sv_apply_gate(sv_state* s, const double* G, const int* targets, int k,
                   const int* controls, int n_controls);
 
+/* ---------------------------------------------------------------------------------------
+ * Batching: one gate pass for many states in one launch (the pass kernel walks the
+ * block-groups of all of them), for serving many small simulations at once.
+ * sv_batch_create: max_states per step; device descriptors come from the pool, host staging
+ *   is pinned memory; all work goes to `stream`, which every state of a step must use.
+ * sv_batch_apply: gates[i] to states[i] for i < count: each state gets one Algorithm 1 pass
+ *   exactly as sv_apply_gate would give it (bit-identical results). States must be compressed,
+ *   of one dtype and one block size, each at most once per call. Asynchronous; each state's
+ *   errors and overflow replay are handled by its own sv_sync.
+ * sv_batch_use_graphs: capture the step (descriptor copy, pass, norm kernels) as CUDA graphs,
+ *   one per batch shape (count, gate width, coupled blocks, groups) and replay them.
+ * ------------------------------------------------------------------------------------- */
+typedef struct {
+  const double* G;      /* row-major 2^k x 2^k complex (re, im) FP64 */
+  const int* targets;
+  int k;
+  const int* controls;
+  int n_controls;
+} sv_gate_t;
+typedef struct sv_batch sv_batch;
+int sv_batch_create(sv_pool* pool, int max_states, void* stream, sv_batch** out);
+int sv_batch_destroy(sv_batch* batch);
+int sv_batch_use_graphs(sv_batch* batch, int on);
+int sv_batch_apply(sv_batch* batch, sv_state* const* states, const sv_gate_t* gates, int count);
+
 /* Wait for the state's stream, resolve arena overflow (grow + replay) and return any
  * error recorded on the device. */
 int sv_sync(sv_state* s);

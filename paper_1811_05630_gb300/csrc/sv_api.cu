@@ -176,9 +176,8 @@ bool gate_args_ok(const sv_state* s, const int* targets, int k, const int* contr
   return true;
 }
 
-// Build the pass arguments of one logged step and launch pass + norm tree + finalize.
-int launch_logged(sv_state* s, const Logged& lg) {
-  PassArgs a;
+// The pass arguments of one logged step.
+void build_args(const sv_state* s, const Logged& lg, PassArgs& a) {
   std::memset(&a, 0, sizeof(a));
   a.b = s->b;
   a.nv = 2 << s->b;
@@ -251,6 +250,12 @@ int launch_logged(sv_state* s, const Logged& lg) {
     }
   }
   a.ngroups = s->nblocks >> a.h;
+}
+
+// Launch pass + norm tree + finalize for one logged step of one state.
+int launch_logged(sv_state* s, const Logged& lg) {
+  PassArgs a;
+  build_args(s, lg, a);
   std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
   if (s->timing && !lg.basis) {
     if (s->ev_free.empty()) {
@@ -272,6 +277,14 @@ int launch_logged(sv_state* s, const Logged& lg) {
   if (e != cudaSuccess) return cuda_err(e);
   e = launch_finalize(s->sc, s->vroot, s->two2, lg.in_id, lg.seq, s->st);
   return cuda_err(e);
+}
+
+// Record one step in a state's log (after its launch) and flip its arenas.
+int log_step(sv_state* s, Logged&& lg) {
+  s->cur ^= 1;
+  s->log.push_back(std::move(lg));
+  if (s->log.size() >= 256) return sv_sync(s);
+  return SV_OK;
 }
 
 int submit(sv_state* s, Logged lg) {
@@ -761,6 +774,192 @@ int sv_get_pass_timing(sv_state* s, double* kernel_ms, uint64_t* passes, uint64_
   if (passes) *passes = s->timed_passes;
   if (bytes) *bytes = (h.io_bytes - s->io_base) + 32ull * s->nblocks * s->timed_passes;
   return SV_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+constexpr int kRing = 4;
+
+struct GraphKey {
+  int count, kmax, gmax;
+  unsigned long long groups;
+  bool operator<(const GraphKey& o) const {
+    if (count != o.count) return count < o.count;
+    if (kmax != o.kmax) return kmax < o.kmax;
+    if (gmax != o.gmax) return gmax < o.gmax;
+    return groups < o.groups;
+  }
+};
+
+}  // namespace
+
+struct sv_batch {
+  sv_pool* pool = nullptr;
+  cudaStream_t st = nullptr;
+  int max_states = 0;
+  Region dev_r;
+  uint8_t* d_blob = nullptr;
+  size_t blob_bytes = 0;
+  size_t off_prefix = 0, off_trees = 0, off_nb = 0;
+  uint8_t* h_buf[kRing] = {nullptr};
+  cudaEvent_t h_done[kRing] = {nullptr};
+  int ring = 0;
+  bool graphs = false;
+  std::map<GraphKey, std::vector<cudaGraphExec_t>> cache;
+  std::map<GraphKey, int> seen;  // shapes run once uncaptured (their kernels are set up)
+  unsigned long long steps = 0;
+};
+
+extern "C" {
+
+int sv_batch_create(sv_pool* pool, int max_states, void* stream, sv_batch** out) {
+  if (!pool || !out || max_states < 1 || max_states > 65536) return SV_ERR_ARG;
+  sv_batch* bt = new sv_batch();
+  bt->pool = pool;
+  bt->st = (cudaStream_t)stream;
+  bt->max_states = max_states;
+  size_t off = (size_t)max_states * sizeof(PassArgs);
+  bt->off_prefix = off;
+  off += round_up((size_t)(max_states + 1) * 8, 256);
+  bt->off_trees = off;
+  off += round_up((size_t)max_states * 8, 256);
+  bt->off_nb = off;
+  off += round_up((size_t)max_states * 8, 256);
+  bt->blob_bytes = off;
+  if (!region_alloc(pool, &bt->dev_r, off)) {
+    delete bt;
+    return SV_ERR_OOM;
+  }
+  bt->d_blob = pool_ptr(pool, bt->dev_r.off);
+  for (int r = 0; r < kRing; ++r) {
+    if (cudaHostAlloc((void**)&bt->h_buf[r], off, cudaHostAllocDefault) != cudaSuccess ||
+        cudaEventCreateWithFlags(&bt->h_done[r], cudaEventDisableTiming) != cudaSuccess) {
+      sv_batch_destroy(bt);
+      return SV_ERR_CUDA;
+    }
+  }
+  pool->nstates++;
+  *out = bt;
+  return SV_OK;
+}
+
+int sv_batch_destroy(sv_batch* bt) {
+  if (!bt) return SV_ERR_ARG;
+  cudaStreamSynchronize(bt->st);
+  for (auto& kv : bt->cache)
+    for (auto g : kv.second) cudaGraphExecDestroy(g);
+  for (int r = 0; r < kRing; ++r) {
+    if (bt->h_buf[r]) cudaFreeHost(bt->h_buf[r]);
+    if (bt->h_done[r]) cudaEventDestroy(bt->h_done[r]);
+  }
+  if (bt->dev_r.live) {
+    region_free(bt->pool, &bt->dev_r);
+    bt->pool->nstates--;
+  }
+  delete bt;
+  return SV_OK;
+}
+
+int sv_batch_use_graphs(sv_batch* bt, int on) {
+  if (!bt) return SV_ERR_ARG;
+  bt->graphs = on != 0;
+  return SV_OK;
+}
+
+int sv_batch_apply(sv_batch* bt, sv_state* const* states, const sv_gate_t* gates, int count) {
+  if (!bt || !states || !gates || count < 1 || count > bt->max_states) return SV_ERR_ARG;
+  const sv_state* s0 = states[0];
+  if (!s0) return SV_ERR_ARG;
+  for (int i = 0; i < count; ++i) {
+    const sv_state* s = states[i];
+    const sv_gate_t& g = gates[i];
+    if (!s || s->plain || s->dtype != s0->dtype || s->b != s0->b || s->st != bt->st || !g.G ||
+        !gate_args_ok(s, g.targets, g.k, g.controls, g.n_controls))
+      return SV_ERR_ARG;
+    for (int j = 0; j < i; ++j)
+      if (states[j] == s) return SV_ERR_ARG;  // one gate per state per step
+    int nh = 0;
+    for (int l = 0; l < g.k; ++l) nh += g.targets[l] >= s->b;
+    if (nh > 2) return SV_ERR_UNSUPPORTED;
+  }
+  // stage descriptors and tables in the next pinned buffer of the ring
+  const int slot = bt->ring;
+  bt->ring = (bt->ring + 1) % kRing;
+  cudaError_t e = cudaEventSynchronize(bt->h_done[slot]);  // its previous copy has run
+  if (e != cudaSuccess) return cuda_err(e);
+  uint8_t* hb = bt->h_buf[slot];
+  PassArgs* hd = (PassArgs*)hb;
+  unsigned long long* hp = (unsigned long long*)(hb + bt->off_prefix);
+  const double** ht = (const double**)(hb + bt->off_trees);
+  unsigned long long* hn = (unsigned long long*)(hb + bt->off_nb);
+  std::vector<Logged> logs((size_t)count);
+  int kmax = 1, gmax = 1;
+  hp[0] = 0;
+  for (int i = 0; i < count; ++i) {
+    sv_state* s = states[i];
+    const sv_gate_t& g = gates[i];
+    Logged& lg = logs[(size_t)i];
+    lg.G.assign(g.G, g.G + 2 * (1 << g.k) * (1 << g.k));
+    lg.targets.assign(g.targets, g.targets + g.k);
+    if (g.n_controls) lg.controls.assign(g.controls, g.controls + g.n_controls);
+    lg.seq = s->seq++;
+    lg.in_id = s->cur;
+    lg.out_id = s->cur ^ 1;
+    build_args(s, lg, hd[i]);
+    hp[i + 1] = hp[i] + hd[i].ngroups;
+    ht[i] = s->tree;
+    hn[i] = s->nblocks;
+    kmax = std::max(kmax, hd[i].K);
+    gmax = std::max(gmax, hd[i].G);
+  }
+  const int kbucket = kmax <= 2 ? 2 : (kmax <= 4 ? 4 : 8);
+  const PassArgs* d_descs = (const PassArgs*)bt->d_blob;
+  const unsigned long long* d_prefix = (const unsigned long long*)(bt->d_blob + bt->off_prefix);
+  const double* const* d_trees = (const double* const*)(bt->d_blob + bt->off_trees);
+  const unsigned long long* d_nb = (const unsigned long long*)(bt->d_blob + bt->off_nb);
+  auto enqueue = [&](uint8_t* src) -> cudaError_t {
+    cudaError_t r = cudaMemcpyAsync(bt->d_blob, src, bt->blob_bytes, cudaMemcpyHostToDevice, bt->st);
+    if (r == cudaSuccess)
+      r = launch_pass_batch(d_descs, d_prefix, count, hp[count], s0->b, gmax, kbucket,
+                            s0->dtype == SV_C64 ? 1 : 2, bt->st);
+    if (r == cudaSuccess) r = launch_norm_batch(d_descs, d_trees, d_nb, count, bt->st);
+    return r;
+  };
+  GraphKey key{count, kbucket, gmax, hp[count]};
+  auto it = bt->cache.find(key);
+  const bool seen_before = bt->seen[key]++ > 0;
+  if (bt->graphs && it == bt->cache.end() && seen_before) {
+    // capture one graph per ring slot (each copies from its own pinned buffer)
+    std::vector<cudaGraphExec_t> execs;
+    for (int r = 0; r < kRing && e == cudaSuccess; ++r) {
+      cudaGraph_t graph = nullptr;
+      e = cudaStreamBeginCapture(bt->st, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        cudaError_t e2 = enqueue(bt->h_buf[r]);
+        e = cudaStreamEndCapture(bt->st, &graph);
+        if (e == cudaSuccess) e = e2;
+      }
+      cudaGraphExec_t ex = nullptr;
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, graph, 0);
+      if (graph) cudaGraphDestroy(graph);
+      if (e == cudaSuccess) execs.push_back(ex);
+    }
+    if (e != cudaSuccess) return cuda_err(e);
+    it = bt->cache.emplace(key, std::move(execs)).first;
+  }
+  if (bt->graphs && it != bt->cache.end()) e = cudaGraphLaunch(it->second[(size_t)slot], bt->st);
+  else e = enqueue(hb);
+  if (e == cudaSuccess) e = cudaEventRecord(bt->h_done[slot], bt->st);
+  if (e != cudaSuccess) return cuda_err(e);
+  bt->steps++;
+  int rc = SV_OK;
+  for (int i = 0; i < count; ++i) {
+    const int r = log_step(states[i], std::move(logs[(size_t)i]));
+    if (r && !rc) rc = r;
+  }
+  return rc;
 }
 
 int sv_overlap_qft(sv_state* s, uint64_t x, double* out) {

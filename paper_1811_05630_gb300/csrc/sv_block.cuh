@@ -19,6 +19,7 @@ struct Misc {
   unsigned long long red[40];
   int vin_cnt[4], vout_cnt[4];
   unsigned int err;
+  int live;  // the state being processed is not poisoned
   int D;
   int nesc;
   int cnt;
@@ -30,6 +31,36 @@ struct Misc {
   int first[34];   // canonical first code per length
   int offs[34];    // first canonical index per length
   int lcount[34];  // codes per length
+};
+
+struct __align__(16) PassArgs {
+  int b, nv, G, h, k, K, nlow;
+  int low_t[5];       // low targets ascending (for base enumeration)
+  int high_pos[5];    // (high target - b) ascending (block-id expansion)
+  int slot_shift[5];  // for slot bit l (target order of high targets): block-id bit
+  int pos_delta[8];   // value-position offset of tuple member m within the group
+  unsigned long long cmask;
+  int apply_gate;     // 0: identity (initial compression)
+  int input_basis;    // 1: the input is the basis state |basis>
+  unsigned long long basis;
+  int use_sigma;
+  double g[2 * 64];   // gate matrix (re, im), row-major K x K
+  float gf[2 * 64];
+  QuantP qp;
+  double two2;
+  double two_r;       // fl(2eb * r), the dequantize-requantize factor (about 1)
+  unsigned long long ngroups;
+  const uint8_t* in_arena;
+  const unsigned long long* in_off;
+  const unsigned int* in_len;
+  uint8_t* out_arena;
+  unsigned long long out_cap;
+  int out_id;
+  unsigned long long* out_off;
+  unsigned int* out_len;
+  DevScalars* sc;
+  double* vsum;
+  unsigned int seq;
 };
 
 // Fixed-point form of one gate pass for complex128 (computed once per CTA): output jj, part
@@ -48,7 +79,7 @@ struct FastGate {
 struct Layout {
   int nv, G, hs, dcap, p2cap;
   uint32_t off_q, off_vin_pos, off_vin_bits, off_vout_pos, off_vout_bits, off_hkey, off_hval,
-      off_stage, off_build, off_misc, off_fast, total;
+      off_stage, off_build, off_misc, off_fast, off_desc, total;
   uint32_t stage_bytes, build_bytes;
   uint32_t sort_off, sort_n;  // rank-sort scratch inside the build area
   uint32_t off_wint, off_parent, off_parent2, off_lens, off_lens2;
@@ -106,6 +137,8 @@ __host__ __device__ inline Layout make_layout(int b, int G, int csize) {
   o += (uint32_t)pad_to(sizeof(Misc), 16);  // scalars and scan workspace
   L.off_fast = o;
   o += (uint32_t)pad_to(sizeof(FastGate), 16);
+  L.off_desc = o;  // the batched pass keeps the current state's descriptor here
+  o += (uint32_t)pad_to(sizeof(PassArgs), 16);
   L.total = o;
   return L;
 }
@@ -118,36 +151,6 @@ __host__ __device__ inline int worker_threads(int b) {
   if (t < 32) t = 32;
   return t;
 }
-
-struct PassArgs {
-  int b, nv, G, h, k, K, nlow;
-  int low_t[5];       // low targets ascending (for base enumeration)
-  int high_pos[5];    // (high target - b) ascending (block-id expansion)
-  int slot_shift[5];  // for slot bit l (target order of high targets): block-id bit
-  int pos_delta[8];   // value-position offset of tuple member m within the group
-  unsigned long long cmask;
-  int apply_gate;     // 0: identity (initial compression)
-  int input_basis;    // 1: the input is the basis state |basis>
-  unsigned long long basis;
-  int use_sigma;
-  double g[2 * 64];   // gate matrix (re, im), row-major K x K
-  float gf[2 * 64];
-  QuantP qp;
-  double two2;
-  double two_r;       // fl(2eb * r), the dequantize-requantize factor (about 1)
-  unsigned long long ngroups;
-  const uint8_t* in_arena;
-  const unsigned long long* in_off;
-  const unsigned int* in_len;
-  uint8_t* out_arena;
-  unsigned long long out_cap;
-  int out_id;
-  unsigned long long* out_off;
-  unsigned int* out_len;
-  DevScalars* sc;
-  double* vsum;
-  unsigned int seq;
-};
 
 template <typename Real>
 struct Worker {

@@ -9,6 +9,13 @@ namespace sv {
 
 // Fused gate pass (Algorithm 1 over every slice) for one state; Real by dtype (1 = float).
 cudaError_t launch_pass(const PassArgs& a, int dtype, cudaStream_t st);
+// The fused pass over the block-groups of many states (one descriptor each), and the
+// batched norm finalization (verbatim-sum tree per state in one CTA, then N and sigma).
+cudaError_t launch_pass_batch(const PassArgs* descs, const unsigned long long* gprefix, int nstates,
+                              unsigned long long total_groups, int b, int Gmax, int Kmax, int dtype,
+                              cudaStream_t st);
+cudaError_t launch_norm_batch(const PassArgs* descs, const double* const* trees, const unsigned long long* nblocks,
+                              int nstates, cudaStream_t st);
 // Pairwise (level by level) sum of n = 2^k per-block verbatim sums into root[0].
 cudaError_t launch_vsum_tree(const double* vsum, unsigned long long n, double* scratch,
                              double* root, const DevScalars* sc, cudaStream_t st);

@@ -195,10 +195,124 @@ __device__ __forceinline__ void tuple_exact(Worker<Real>& w, const PassArgs& a, 
 // Algorithm 1: for the gate G, for every slice: Decompress, Normalize, GateComputation,
 // Compress. One CTA per group of 2^h coupled blocks (grid-stride over the groups).
 // ---------------------------------------------------------------------------------------
+// One group of 2^h coupled blocks of one state: Decompress, Normalize + GateComputation,
+// Compress (shared by the single-state and the batched pass kernels).
+template <typename Real, int KM>
+__device__ __forceinline__ void pass_group(Worker<Real>& w, const PassArgs& a, const FastGate* fg,
+                                           double sigma, unsigned long long grp) {
+  using A = Arith<Real>;
+  const Layout& L = w.L;
+  const Real sg = (Real)sigma;  // complex64: sigma rounded to float once
+  const int B = L.nv / 2;
+  constexpr bool kFast = sizeof(Real) == 8;
+  unsigned long long base = grp;
+  for (int l = 0; l < a.h; ++l) base = insert_zero_bit(base, a.high_pos[l]);
+  unsigned long long blks[4];
+  for (int g = 0; g < a.G; ++g) {
+    unsigned long long bid = base;
+    for (int l = 0; l < a.h; ++l)
+      if ((g >> l) & 1) bid |= 1ull << a.slot_shift[l];
+    blks[g] = bid;
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) w.vout_cnt[threadIdx.x] = 0;
+  // ---- Decompress(S) ----
+  for (int g = 0; g < a.G; ++g) {
+    if (a.input_basis) {
+      const int pos = ((a.basis >> a.b) == blks[g]) ? 2 * (int)(a.basis & (unsigned long long)(B - 1)) : -1;
+      w.load_basis(g, pos);
+    } else {
+      w.decode(g, a.in_arena + a.in_off[blks[g]], a.in_len[blks[g]]);
+    }
+  }
+  // ---- Normalize(S) and GateComputation(G, S), tuple by tuple, in place ----
+  const int ntup = B >> a.nlow;
+  for (int u = threadIdx.x; u < ntup; u += blockDim.x) {
+    unsigned long long o = (unsigned long long)u;
+    for (int l = 0; l < a.nlow; ++l) o = insert_zero_bit(o, a.low_t[l]);
+    const unsigned long long gidx = (blks[0] << a.b) | o;
+    const bool ctrl = a.apply_gate && ((gidx & a.cmask) == a.cmask);
+    const int bp = 2 * (int)o;
+    if (kFast && fg->F >= 0) {
+      int32_t qv[2 * KM];
+      int gq[KM], jq[KM];
+      bool sentinel = false;
+#pragma unroll
+      for (int mm = 0; mm < KM; ++mm)
+        if (mm < a.K) {
+          const int p = bp + a.pos_delta[mm];
+          gq[mm] = p / L.nv;
+          jq[mm] = p - gq[mm] * L.nv;
+          qv[2 * mm] = w.q[p];
+          qv[2 * mm + 1] = w.q[p + 1];
+          sentinel |= qv[2 * mm] == kSentinel || qv[2 * mm + 1] == kSentinel;
+        }
+      if (!sentinel) {
+        const int F = fg->F;
+        const long long margin = fg->margin;
+        int32_t out[2 * KM];
+        unsigned int exact_mask = 0;
+#pragma unroll
+        for (int jj = 0; jj < KM; ++jj)
+          if (jj < a.K) {
+#pragma unroll
+            for (int p = 0; p < 2; ++p) {
+              long long sh = 0, sl = 0;
+              if (ctrl && fg->diag) {
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                  const long long qq = qv[2 * jj + c];
+                  sh += qq * fg->chi[jj][p][jj][c];
+                  sl += (qq * fg->clo[jj][p][jj][c]) >> 4;
+                }
+              } else if (ctrl) {
+#pragma unroll
+                for (int m = 0; m < KM; ++m)
+                  if (m < a.K) {
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) {
+                      const long long qq = qv[2 * m + c];
+                      sh += qq * fg->chi[jj][p][m][c];
+                      sl += (qq * fg->clo[jj][p][m][c]) >> 4;
+                    }
+                  }
+              } else {
+                const long long qq = qv[2 * jj + p];
+                sh = qq * fg->idhi;
+                sl = (qq * fg->idlo) >> 4;
+              }
+              if (!fast_round(sh + (sl >> 27), F, margin, &out[2 * jj + p])) exact_mask |= 1u << (2 * jj + p);
+            }
+          }
+        double zx[2 * KM];
+        if (exact_mask) {
+#pragma unroll
+          for (int e = 0; e < 2 * KM; ++e)
+            if ((exact_mask >> e) & 1u) zx[e] = exact_component(a, sigma, qv, e >> 1, e & 1, ctrl);
+        }
+#pragma unroll
+        for (int mm = 0; mm < KM; ++mm)
+          if (mm < a.K) {
+#pragma unroll
+            for (int p = 0; p < 2; ++p) {
+              const int e = 2 * mm + p;
+              if ((exact_mask >> e) & 1u) w.put_value(gq[mm], jq[mm] + p, (Real)zx[e]);
+              else w.q[gq[mm] * L.nv + jq[mm] + p] = out[e];
+            }
+          }
+        continue;
+      }
+    }
+    tuple_exact<Real, KM>(w, a, sg, bp, ctrl);
+  }
+  __syncthreads();
+  // ---- Compress(S) ----
+  for (int g = 0; g < a.G; ++g) w.encode(g, blks[g], a);
+}
+
 template <typename Real, int KM>
 __global__ void __launch_bounds__(256) k_pass(const PassArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  using A = Arith<Real>;
   const Layout L = make_layout(a.b, a.G, (int)sizeof(Real));
   Worker<Real> w;
   w.init(smem, L, a.b, a.qp);
@@ -206,125 +320,107 @@ __global__ void __launch_bounds__(256) k_pass(const PassArgs a) {
   // thread reads the flag so that the whole CTA takes the same branch.
   if (threadIdx.x == 0) {
     w.m->err = 0;
-    w.m->ok = *(volatile unsigned int*)&a.sc->status == 0;
+    w.m->live = *(volatile unsigned int*)&a.sc->status == 0;
   }
   __syncthreads();
-  if (!w.m->ok) return;
+  if (!w.m->live) return;
   const double sigma = a.use_sigma ? *(volatile double*)&a.sc->sigma : 1.0;
-  const Real sg = (Real)sigma;  // complex64: sigma rounded to float once
-  const int B = L.nv / 2;
   FastGate* fg = (FastGate*)(smem + L.off_fast);
-  constexpr bool kFast = sizeof(Real) == 8;
-  if (kFast && threadIdx.x == 0) fast_prepare(fg, a, sigma);  // visible after the loop's barrier
-  for (unsigned long long grp = blockIdx.x; grp < a.ngroups; grp += gridDim.x) {
-    unsigned long long base = grp;
-    for (int l = 0; l < a.h; ++l) base = insert_zero_bit(base, a.high_pos[l]);
-    unsigned long long blks[4];
-    for (int g = 0; g < a.G; ++g) {
-      unsigned long long bid = base;
-      for (int l = 0; l < a.h; ++l)
-        if ((g >> l) & 1) bid |= 1ull << a.slot_shift[l];
-      blks[g] = bid;
-    }
-    __syncthreads();
-    if (threadIdx.x < 4) w.vout_cnt[threadIdx.x] = 0;
-    // ---- Decompress(S) ----
-    for (int g = 0; g < a.G; ++g) {
-      if (a.input_basis) {
-        const int pos = ((a.basis >> a.b) == blks[g]) ? 2 * (int)(a.basis & (unsigned long long)(B - 1)) : -1;
-        w.load_basis(g, pos);
-      } else {
-        w.decode(g, a.in_arena + a.in_off[blks[g]], a.in_len[blks[g]]);
-      }
-    }
-    // ---- Normalize(S) and GateComputation(G, S), tuple by tuple, in place ----
-    const int ntup = B >> a.nlow;
-    for (int u = threadIdx.x; u < ntup; u += blockDim.x) {
-      unsigned long long o = (unsigned long long)u;
-      for (int l = 0; l < a.nlow; ++l) o = insert_zero_bit(o, a.low_t[l]);
-      const unsigned long long gidx = (blks[0] << a.b) | o;
-      const bool ctrl = a.apply_gate && ((gidx & a.cmask) == a.cmask);
-      const int bp = 2 * (int)o;
-      if (kFast && fg->F >= 0) {
-        int32_t qv[2 * KM];
-        int gq[KM], jq[KM];
-        bool sentinel = false;
-#pragma unroll
-        for (int mm = 0; mm < KM; ++mm)
-          if (mm < a.K) {
-            const int p = bp + a.pos_delta[mm];
-            gq[mm] = p / L.nv;
-            jq[mm] = p - gq[mm] * L.nv;
-            qv[2 * mm] = w.q[p];
-            qv[2 * mm + 1] = w.q[p + 1];
-            sentinel |= qv[2 * mm] == kSentinel || qv[2 * mm + 1] == kSentinel;
-          }
-        if (!sentinel) {
-          const int F = fg->F;
-          const long long margin = fg->margin;
-          int32_t out[2 * KM];
-          unsigned int exact_mask = 0;
-#pragma unroll
-          for (int jj = 0; jj < KM; ++jj)
-            if (jj < a.K) {
-#pragma unroll
-              for (int p = 0; p < 2; ++p) {
-                long long sh = 0, sl = 0;
-                if (ctrl && fg->diag) {
-#pragma unroll
-                  for (int c = 0; c < 2; ++c) {
-                    const long long qq = qv[2 * jj + c];
-                    sh += qq * fg->chi[jj][p][jj][c];
-                    sl += (qq * fg->clo[jj][p][jj][c]) >> 4;
-                  }
-                } else if (ctrl) {
-#pragma unroll
-                  for (int m = 0; m < KM; ++m)
-                    if (m < a.K) {
-#pragma unroll
-                      for (int c = 0; c < 2; ++c) {
-                        const long long qq = qv[2 * m + c];
-                        sh += qq * fg->chi[jj][p][m][c];
-                        sl += (qq * fg->clo[jj][p][m][c]) >> 4;
-                      }
-                    }
-                } else {
-                  const long long qq = qv[2 * jj + p];
-                  sh = qq * fg->idhi;
-                  sl = (qq * fg->idlo) >> 4;
-                }
-                if (!fast_round(sh + (sl >> 27), F, margin, &out[2 * jj + p])) exact_mask |= 1u << (2 * jj + p);
-              }
-            }
-          double zx[2 * KM];
-          if (exact_mask) {
-#pragma unroll
-            for (int e = 0; e < 2 * KM; ++e)
-              if ((exact_mask >> e) & 1u) zx[e] = exact_component(a, sigma, qv, e >> 1, e & 1, ctrl);
-          }
-#pragma unroll
-          for (int mm = 0; mm < KM; ++mm)
-            if (mm < a.K) {
-#pragma unroll
-              for (int p = 0; p < 2; ++p) {
-                const int e = 2 * mm + p;
-                if ((exact_mask >> e) & 1u) w.put_value(gq[mm], jq[mm] + p, (Real)zx[e]);
-                else w.q[gq[mm] * L.nv + jq[mm] + p] = out[e];
-              }
-            }
-          continue;
-        }
-      }
-      tuple_exact<Real, KM>(w, a, sg, bp, ctrl);
-    }
-    __syncthreads();
-    // ---- Compress(S) ----
-    for (int g = 0; g < a.G; ++g) w.encode(g, blks[g], a);
-  }
+  if (sizeof(Real) == 8 && threadIdx.x == 0) fast_prepare(fg, a, sigma);  // visible after pass_group's barrier
+  for (unsigned long long grp = blockIdx.x; grp < a.ngroups; grp += gridDim.x)
+    pass_group<Real, KM>(w, a, fg, sigma, grp);
   if (threadIdx.x == 0 && w.m->err) {
     atomicOr(&a.sc->status, w.m->err);
     atomicMin(&a.sc->fail_seq, a.seq);
   }
+}
+
+
+// The same pass for a batch of states (one gate each; equal dtype and block size). Group g of
+// the launch belongs to the state s with gprefix[s] <= g < gprefix[s+1]; a CTA copies that
+// state's descriptor into shared memory when it reaches the state's first group.
+template <typename Real, int KM>
+__global__ void __launch_bounds__(256) k_pass_batch(const PassArgs* __restrict__ descs,
+                                                    const unsigned long long* __restrict__ gprefix,
+                                                    int nstates, int b, int Gmax) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const Layout L = make_layout(b, Gmax, (int)sizeof(Real));
+  PassArgs* as = (PassArgs*)(smem + L.off_desc);
+  Worker<Real> w;
+  QuantP q0{0.0, 0.0, 0.0};
+  w.init(smem, L, b, q0);
+  FastGate* fg = (FastGate*)(smem + L.off_fast);
+  const unsigned long long total = gprefix[nstates];
+  int cur = -1;
+  double sigma = 1.0;
+  for (unsigned long long g = blockIdx.x; g < total; g += gridDim.x) {
+    int lo = 0, hi = nstates;  // largest s with gprefix[s] <= g
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (gprefix[mid] <= g) lo = mid;
+      else hi = mid;
+    }
+    if (lo != cur) {
+      __syncthreads();
+      if (cur >= 0 && threadIdx.x == 0 && w.m->err) {
+        atomicOr(&as->sc->status, w.m->err);
+        atomicMin(&as->sc->fail_seq, as->seq);
+      }
+      __syncthreads();
+      const uint4* src = (const uint4*)(descs + lo);
+      uint4* dst = (uint4*)as;
+      for (int i = threadIdx.x; i < (int)(sizeof(PassArgs) / 16); i += blockDim.x) dst[i] = src[i];
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        w.m->err = 0;
+        w.m->live = *(volatile unsigned int*)&as->sc->status == 0;
+      }
+      __syncthreads();
+      cur = lo;
+      w.qp = as->qp;
+      sigma = as->use_sigma ? *(volatile double*)&as->sc->sigma : 1.0;
+      if (w.m->live && sizeof(Real) == 8 && threadIdx.x == 0) fast_prepare(fg, *as, sigma);
+    }
+    if (!w.m->live) continue;
+    pass_group<Real, KM>(w, *as, fg, sigma, g - gprefix[lo]);
+  }
+  __syncthreads();
+  if (cur >= 0 && threadIdx.x == 0 && w.m->err) {
+    atomicOr(&as->sc->status, w.m->err);
+    atomicMin(&as->sc->fail_seq, as->seq);
+  }
+}
+
+template <typename Real, int KM>
+static cudaError_t launch_pass_batch_k(const PassArgs* descs, const unsigned long long* gprefix, int nstates,
+                                       unsigned long long total_groups, int b, int Gmax, cudaStream_t st) {
+  const Layout L = make_layout(b, Gmax, (int)sizeof(Real));
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_pass_batch<Real, KM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  if (L.total > 227 * 1024) return cudaErrorInvalidValue;
+  const int T = worker_threads(b);
+  unsigned long long grid = total_groups;
+  if (grid > 0x7fffffffull) grid = 0x7fffffffull;
+  if (grid == 0) return cudaSuccess;
+  k_pass_batch<Real, KM><<<(unsigned int)grid, T, L.total, st>>>(descs, gprefix, nstates, b, Gmax);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pass_batch(const PassArgs* descs, const unsigned long long* gprefix, int nstates,
+                              unsigned long long total_groups, int b, int Gmax, int Kmax, int dtype,
+                              cudaStream_t st) {
+  if (dtype == 1) {
+    if (Kmax <= 2) return launch_pass_batch_k<float, 2>(descs, gprefix, nstates, total_groups, b, Gmax, st);
+    if (Kmax <= 4) return launch_pass_batch_k<float, 4>(descs, gprefix, nstates, total_groups, b, Gmax, st);
+    return launch_pass_batch_k<float, 8>(descs, gprefix, nstates, total_groups, b, Gmax, st);
+  }
+  if (Kmax <= 2) return launch_pass_batch_k<double, 2>(descs, gprefix, nstates, total_groups, b, Gmax, st);
+  if (Kmax <= 4) return launch_pass_batch_k<double, 4>(descs, gprefix, nstates, total_groups, b, Gmax, st);
+  return launch_pass_batch_k<double, 8>(descs, gprefix, nstates, total_groups, b, Gmax, st);
 }
 
 template <typename Real, int KM>
@@ -429,6 +525,85 @@ __global__ void k_finalize(DevScalars* sc, const double* root, double two2, int 
 cudaError_t launch_finalize(DevScalars* sc, const double* root, double two2, int reset_id,
                             unsigned int seq, cudaStream_t st) {
   k_finalize<<<1, 32, 0, st>>>(sc, root, two2, reset_id, seq);
+  return cudaGetLastError();
+}
+
+// Batched norm finalization: one CTA per state computes that state's pairwise verbatim sum
+// (chunks of 2048 level by level, the same tree as the multi-launch version) when the pass
+// stored a verbatim value; then one thread per state finalizes N and sigma.
+__global__ void __launch_bounds__(1024) k_vsum_batch(const PassArgs* __restrict__ descs,
+                                                     const double* const* __restrict__ trees,
+                                                     const unsigned long long* __restrict__ nblocks) {
+  const PassArgs& a = descs[blockIdx.x];
+  if (a.sc->acc.n_verbatim == 0 || a.sc->status) return;
+  __shared__ double sm[2048];
+  double* tree = (double*)trees[blockIdx.x];
+  const double* in = a.vsum;
+  unsigned long long n = nblocks[blockIdx.x];
+  double* bufs[2] = {tree, tree + (n / 2048 + 1)};
+  int which = 0;
+  double* out = bufs[0];
+  while (true) {
+    const unsigned long long chunk = n < 2048 ? n : 2048;
+    const unsigned long long nch = n / chunk;
+    out = bufs[which];
+    for (unsigned long long c = 0; c < nch; ++c) {
+      for (unsigned long long i = threadIdx.x; i < chunk; i += blockDim.x) sm[i] = in[c * chunk + i];
+      __syncthreads();
+      for (unsigned long long cnt = chunk; cnt > 1; cnt >>= 1) {
+        const unsigned long long half = cnt >> 1;
+        double v = 0.0;
+        if (threadIdx.x < half) v = __dadd_rn(sm[2 * threadIdx.x], sm[2 * threadIdx.x + 1]);
+        __syncthreads();
+        if (threadIdx.x < half) sm[threadIdx.x] = v;
+        __syncthreads();
+      }
+      if (threadIdx.x == 0) out[c] = sm[0];
+      __syncthreads();
+    }
+    if (nch == 1) break;
+    in = out;
+    which ^= 1;
+    n = nch;
+  }
+  if (threadIdx.x == 0) tree[0] = out[0];  // the root, wherever the last level left it
+}
+
+__global__ void k_finalize_batch(const PassArgs* __restrict__ descs, const double* const* __restrict__ trees,
+                                 int nstates) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nstates) return;
+  const PassArgs& a = descs[i];
+  DevScalars* sc = a.sc;
+  if (sc->status) return;
+  const double V = sc->acc.n_verbatim ? trees[i][0] : 0.0;
+  const double Sd = __dadd_rn(__dmul_rn(__ull2double_rn(sc->acc.sq_hi), 18446744073709551616.0),
+                              __ull2double_rn(sc->acc.sq_lo));
+  const double N = __dadd_rn(__dmul_rn(Sd, a.two2), V);
+  if (!(N > 0.0) || isinf(N)) {
+    sc->status |= kStNorm;
+    if (a.seq < sc->fail_seq) sc->fail_seq = a.seq;
+    return;
+  }
+  const int reset_id = a.out_id ^ 1;
+  sc->norm = N;
+  sc->sigma = __ddiv_rn(1.0, __dsqrt_rn(N));
+  sc->last = sc->acc;
+  sc->last_bytes = sc->bump[reset_id ^ 1];
+  sc->io_bytes += sc->bump[reset_id] + sc->bump[reset_id ^ 1];
+  sc->acc.sq_lo = sc->acc.sq_hi = 0;
+  sc->acc.n_verbatim = sc->acc.n_escape = 0;
+  sc->acc.modes[0] = sc->acc.modes[1] = sc->acc.modes[2] = 0;
+  sc->bump[reset_id] = 0;
+  sc->pass_index++;
+}
+
+cudaError_t launch_norm_batch(const PassArgs* descs, const double* const* trees, const unsigned long long* nblocks,
+                              int nstates, cudaStream_t st) {
+  k_vsum_batch<<<nstates, 1024, 0, st>>>(descs, trees, nblocks);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_finalize_batch<<<(nstates + 63) / 64, 64, 0, st>>>(descs, trees, nstates);
   return cudaGetLastError();
 }
 

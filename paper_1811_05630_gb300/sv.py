@@ -51,6 +51,11 @@ class Stats(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class GateT(ctypes.Structure):
+    _fields_ = [("G", ctypes.c_void_p), ("targets", ctypes.c_void_p), ("k", ctypes.c_int),
+                ("controls", ctypes.c_void_p), ("n_controls", ctypes.c_int)]
+
+
 _vp, _i, _d, _sz, _u64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t, ctypes.c_uint64
 _P = ctypes.POINTER
 _SIGS = {
@@ -76,6 +81,10 @@ _SIGS = {
     "sv_codec_decompress": ([_vp, _vp, _vp, _u64, _i, _i, _d, _vp, _vp, _vp], _i),
     "sv_codec_compress_static": ([_vp, _u64, _i, _i, _d, _vp, _u64, _vp, _vp, _vp, _P(_u64), _P(_d)], _i),
     "sv_overlap_qft": ([_vp, _u64, _vp], _i),
+    "sv_batch_create": ([_vp, _i, _vp, _P(_vp)], _i),
+    "sv_batch_destroy": ([_vp], _i),
+    "sv_batch_use_graphs": ([_vp, _i], _i),
+    "sv_batch_apply": ([_vp, _vp, _vp, _i], _i),
     "sv_set_pass_timing": ([_vp, _i], _i),
     "sv_get_pass_timing": ([_vp, _P(_d), _P(_u64), _P(_u64)], _i),
     "sv_version": ([], ctypes.c_char_p),
@@ -216,6 +225,40 @@ class State:
         buf = np.zeros(max(ln.value, 1), dtype=np.uint8)
         _check(_L.sv_block_stream(self._h, b, _np_ptr(buf), buf.size, ctypes.byref(ln)), "sv_block_stream")
         return buf[: ln.value].tobytes()
+
+
+class Batch:
+    """Advance many states by one gate each per step, in one launch (optionally replayed
+    from captured CUDA graphs). States must share dtype, block size and this stream."""
+
+    def __init__(self, pool: Pool, max_states: int, stream=None, graphs: bool = False):
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        _check(_L.sv_batch_create(pool.handle, max_states, _stream_handle(self.stream), ctypes.byref(h)),
+               "sv_batch_create")
+        self._h = h
+        self.use_graphs(graphs)
+
+    def use_graphs(self, on: bool):
+        _check(_L.sv_batch_use_graphs(self._h, 1 if on else 0), "sv_batch_use_graphs")
+
+    def apply(self, states, gates):
+        n = len(states)
+        keep = []
+        arr = (GateT * n)()
+        for i, g in enumerate(gates):
+            m = np.ascontiguousarray(g.matrix, dtype=np.complex128)
+            t = np.ascontiguousarray(g.targets, dtype=np.int32)
+            c = np.ascontiguousarray(g.controls if len(g.controls) else [0], dtype=np.int32)
+            keep += [m, t, c]
+            arr[i] = GateT(m.ctypes.data, t.ctypes.data, t.size, c.ctypes.data, len(g.controls))
+        hs = (ctypes.c_void_p * n)(*[s._h.value for s in states])
+        _check(_L.sv_batch_apply(self._h, hs, arr, n), "sv_batch_apply")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _check(_L.sv_batch_destroy(self._h), "sv_batch_destroy")
+            self._h = None
 
 
 def codec_scratch_bytes() -> int:
