@@ -245,7 +245,8 @@ size_t orc_compress_block(const void* values, int block_log2, int dtype, double 
   orc_block_info inf;
   memset(&inf, 0, sizeof(inf));
   u128 sq = 0;
-  double vsum = 0.0;
+  /* squares of the verbatim values (zero elsewhere), summed below by a pairwise tree */
+  double* vsq = (double*)calloc(nv, sizeof(double));
   for (size_t j = 0; j < nv; ++j) {
     double v = load_val(values, dtype, j);
     int32_t qq = 0;
@@ -253,7 +254,7 @@ size_t orc_compress_block(const void* values, int block_log2, int dtype, double 
       verb[j] = 1;
       q[j] = 0;
       inf.n_verbatim++;
-      vsum = vsum + v * v;
+      vsq[j] = v * v;
     } else {
       q[j] = qq;
       sq += (u128)((int64_t)qq * (int64_t)qq);
@@ -272,7 +273,12 @@ size_t orc_compress_block(const void* values, int block_log2, int dtype, double 
   }
   inf.sq_lo = (uint64_t)sq;
   inf.sq_hi = (uint64_t)(sq >> 64);
-  inf.vsum = vsum;
+  /* verbatim part of the block's norm: level-by-level pairwise sum over the 2B values,
+     vsq[i] = vsq[2i] + vsq[2i+1] until one remains (entries of non-verbatim values are +0) */
+  for (size_t cnt = nv; cnt > 1; cnt /= 2)
+    for (size_t i = 0; i < cnt / 2; ++i) vsq[i] = vsq[2 * i] + vsq[2 * i + 1];
+  inf.vsum = vsq[0];
+  free(vsq);
 
   memset(out, 0, orc_block_bound(block_log2, dtype));
   out[1] = (uint8_t)dtype;

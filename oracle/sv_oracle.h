@@ -42,7 +42,7 @@ typedef struct {
   int n_distinct;    /* distinct 16-bit symbols (0 for CONST) */
   uint64_t sq_lo;    /* exact sum of q^2 over non-verbatim values, low 64 bits */
   uint64_t sq_hi;    /* ... high 64 bits */
-  double vsum;       /* sum of x*x over verbatim values, in value order */
+  double vsum;       /* pairwise sum over the block's values of x*x (verbatim) or 0 (others) */
 } orc_block_info;
 
 /* Upper bound of one block stream in bytes. */

@@ -125,3 +125,48 @@ def random_brickwork(n: int, depth: int, seed: int) -> List[Gate]:
 def count_amplitude_updates(n: int, gates: Sequence[Gate]) -> int:
     """Amplitude-updates of a circuit: 2^n per (unfused) gate."""
     return (1 << n) * len(gates)
+
+
+@dataclass
+class Request:
+    rid: int
+    arrival: float          # seconds after the start of the stream
+    kind: str               # "qft" | "grover" | "random"
+    n: int
+    dtype: int              # 1 complex64, 2 complex128
+    eb: float
+    basis: int
+    gates: List[Gate] = field(default_factory=list)
+
+    @property
+    def amp_updates(self) -> int:
+        return (1 << self.n) * len(self.gates)
+
+
+def serving_requests(count: int = 2000, rate: float = 20.0, seed: int = 0, nmin: int = 10,
+                     nmax: int = 28) -> List[Request]:
+    """Seeded Poisson arrivals (mean `rate` per second); each request uniformly one of QFT on
+    a random basis state, Grover with a random marked item and 1-8 iterations, or a random
+    brickwork circuit of depth 4-16; qubits uniform in [nmin, nmax]; complex64 or complex128
+    at equal odds; absolute error bound from {1e-4, 1e-6, 1e-8}."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    t = 0.0
+    out: List[Request] = []
+    for rid in range(count):
+        t += float(rng.exponential(1.0 / rate))
+        kind = ["qft", "grover", "random"][int(rng.integers(3))]
+        n = int(rng.integers(nmin, nmax + 1))
+        dtype = 1 if rng.random() < 0.5 else 2
+        eb = [1e-4, 1e-6, 1e-8][int(rng.integers(3))]
+        sub = int(rng.integers(1 << 62))
+        if kind == "qft":
+            basis = sub & ((1 << n) - 1)
+            gates = qft(n)
+        elif kind == "grover":
+            basis = 0
+            gates = grover(n, sub & ((1 << n) - 1), int(rng.integers(1, 9)))
+        else:
+            basis = 0
+            gates = random_brickwork(n, int(rng.integers(4, 17)), seed=sub)
+        out.append(Request(rid, t, kind, n, dtype, eb, basis, gates))
+    return out

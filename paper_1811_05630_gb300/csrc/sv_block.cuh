@@ -79,7 +79,7 @@ struct FastGate {
 struct Layout {
   int nv, G, hs, dcap, p2cap;
   uint32_t off_q, off_vin_pos, off_vin_bits, off_vout_pos, off_vout_bits, off_hkey, off_hval,
-      off_stage, off_build, off_misc, off_fast, off_desc, total;
+      off_stage, off_build, off_misc, off_fast, off_desc, off_vmask, off_vtree, total;
   uint32_t stage_bytes, build_bytes;
   uint32_t sort_off, sort_n;  // rank-sort scratch inside the build area
   uint32_t off_wint, off_parent, off_parent2, off_lens, off_lens2;
@@ -139,6 +139,10 @@ __host__ __device__ inline Layout make_layout(int b, int G, int csize) {
   o += (uint32_t)pad_to(sizeof(FastGate), 16);
   L.off_desc = o;  // the batched pass keeps the current state's descriptor here
   o += (uint32_t)pad_to(sizeof(PassArgs), 16);
+  L.off_vmask = o;  // complex64: one bit per value marks a verbatim value kept in place
+  o += (uint32_t)pad_to((size_t)G * (L.nv / 32) * 4, 16);
+  L.off_vtree = o;  // pairwise verbatim-square tree across threads
+  o += 256 * 8;
   L.total = o;
   return L;
 }
@@ -164,6 +168,11 @@ struct Worker {
   uint32_t *hkey, *hval, *stage;
   uint8_t* build;
   Misc* m;
+  // complex64 keeps verbatim values in place (float bits in the code slot, flagged here);
+  // complex128 keeps them in the vin/vout lists (at most kVmax per block)
+  static constexpr bool kMask = sizeof(Real) == 4;
+  uint32_t* vmask;
+  double* vtree;
 
   __device__ void init(unsigned char* smem, const Layout& lay, int b_, const QuantP& p) {
     L = lay;
@@ -181,6 +190,8 @@ struct Worker {
     stage = (uint32_t*)(smem + L.off_stage);
     build = smem + L.off_build;
     m = (Misc*)(smem + L.off_misc);
+    vmask = (uint32_t*)(smem + L.off_vmask);
+    vtree = (double*)(smem + L.off_vtree);
     vin_cnt = m->vin_cnt;
     vout_cnt = m->vout_cnt;
   }
@@ -193,11 +204,16 @@ struct Worker {
   __device__ void decode(int g, const uint8_t* s, uint32_t len) {
     const int tid = threadIdx.x, nv = L.nv;
     int32_t* qb = q + g * nv;
-    const bool fits = len >= kHdr && len <= L.stage_bytes && (len & 15) == 0;
+    if (kMask)
+      for (int i = tid; i < (nv >> 5); i += T) vmask[g * (nv >> 5) + i] = 0u;
+    // header and body are staged (they always fit); a complex64 verbatim section can be
+    // longer than the stage and is read from the stream in global memory
+    const bool fits = len >= kHdr && (len & 15) == 0;
+    const uint32_t staged = fits ? (len < (L.stage_bytes & ~15u) ? len : (L.stage_bytes & ~15u)) : 0u;
     if (fits) {
       const uint4* src = (const uint4*)s;
       uint4* dst = (uint4*)stage;
-      for (uint32_t i = tid; i < len / 16; i += T) dst[i] = __ldg(src + i);
+      for (uint32_t i = tid; i < staged / 16; i += T) dst[i] = __ldg(src + i);
     }
     __syncthreads();
     const uint8_t* sm = (const uint8_t*)stage;
@@ -229,7 +245,7 @@ struct Worker {
       if (width > 32 || pbits != (uint32_t)nv * (uint32_t)width) bad = true;
       const uint32_t nwords = (pbits + 31) / 32;
       body_end = kHdr + 4 * nwords;
-      if (body_end > total) bad = true;
+      if (body_end > total || body_end > staged) bad = true;
       if (!bad) {
         const uint32_t* w = (const uint32_t*)(sm + kHdr);
         for (int i = 0; i < vpt; ++i) {
@@ -252,7 +268,7 @@ struct Worker {
       const uint32_t off_pay = off_chunk + (uint32_t)pad_to(2 * C, 4);
       const uint32_t nwords = (pbits + 31) / 32;
       body_end = off_pay + 4 * nwords;
-      if (lmax < 1 || lmax > 24 || D < 1 || D > L.dcap || body_end > total) bad = true;
+      if (lmax < 1 || lmax > 24 || D < 1 || D > L.dcap || body_end > total || body_end > staged) bad = true;
       uint32_t* lut = (uint32_t*)build;
       uint32_t* cstart = (uint32_t*)(build + 4 * (1 << kLutBits));
       const uint16_t* symtab = (const uint16_t*)(sm + off_sym);
@@ -321,18 +337,18 @@ struct Worker {
         }
       }
     // verbatim section: ascending positions, then raw values (aligned to the value size)
-    if (nverb > kVmax) {
+    if (nverb > (kMask ? nv : kVmax)) {
       if (tid == 0) atomicOr(&m->err, kStVerbatim);
     } else if (nverb > 0 && !bad) {
       __syncthreads();
-      read_verbatim(g, sm, body_end, total, nverb);
+      read_verbatim(g, s, body_end, total, nverb);
     }
-    if (tid == 0) vin_cnt[g] = nverb <= kVmax ? nverb : 0;
+    if (tid == 0) vin_cnt[g] = (!kMask && nverb <= kVmax) ? nverb : 0;
     __syncthreads();
   }
 
   __device__ __forceinline__ void read_verbatim(int g, const uint8_t* sm, uint32_t posoff, uint32_t total,
-                                             int nverb) {
+                                                int nverb) {  // sm: the stream in global memory
     const uint32_t valoff = (uint32_t)pad_to(posoff + 2 * nverb, sizeof(Real));
     if (valoff + sizeof(Real) * nverb > total) {
       if (threadIdx.x == 0) atomicOr(&m->err, kStCorrupt);
@@ -345,6 +361,9 @@ struct Worker {
       else bits = ((const uint32_t*)(sm + valoff))[i];
       if (j >= L.nv) {
         atomicOr(&m->err, kStCorrupt);
+      } else if (kMask) {
+        q[g * L.nv + j] = (int32_t)(uint32_t)bits;
+        atomicOr(&vmask[g * (L.nv >> 5) + (j >> 5)], 1u << (j & 31));
       } else {
         vin_pos[g * kVmax + i] = (uint16_t)j;
         vin_bits[g * kVmax + i] = bits;
@@ -419,7 +438,20 @@ struct Worker {
     const int tid = threadIdx.x;
     int32_t* qb = q + g * L.nv;
     for (int j = tid; j < L.nv; j += T) qb[j] = 0;
+    if (kMask)
+      for (int i = tid; i < (L.nv >> 5); i += T) vmask[g * (L.nv >> 5) + i] = 0u;
     __syncthreads();
+    if (kMask) {
+      if (tid == 0) {
+        vin_cnt[g] = 0;
+        if (pos >= 0) {  // the value 1.0, given raw
+          qb[pos] = (int32_t)RawBits<Real>::to((Real)1.0);
+          vmask[g * (L.nv >> 5) + (pos >> 5)] |= 1u << (pos & 31);
+        }
+      }
+      __syncthreads();
+      return;
+    }
     if (tid == 0) {
       if (pos >= 0) {
         qb[pos] = kSentinel;
@@ -433,8 +465,18 @@ struct Worker {
     __syncthreads();
   }
 
+  __device__ __forceinline__ bool is_verb(int g, int j) const {
+    return kMask && ((vmask[g * (L.nv >> 5) + (j >> 5)] >> (j & 31)) & 1u);
+  }
+
+  // code of value j for prediction (verbatim values count as 0)
+  __device__ __forceinline__ int32_t code(int g, int j) const {
+    return is_verb(g, j) ? 0 : q[g * L.nv + j];
+  }
+
   __device__ Real value_at(int g, int j) const {
     const int32_t c = q[g * L.nv + j];
+    if (kMask) return is_verb(g, j) ? RawBits<Real>::from((uint32_t)c) : dequant<Real>(c, qp);
     if (c != kSentinel) return dequant<Real>(c, qp);
     const int n = vin_cnt[g];
     for (int i = 0; i < n; ++i)
@@ -459,6 +501,17 @@ struct Worker {
   // Quantize one result into slot g position j (Compress(S), first step).
   __device__ void put_value(int g, int j, Real v) {
     int32_t c;
+    if (kMask) {
+      uint32_t* w = &vmask[g * (L.nv >> 5) + (j >> 5)];
+      if (quantize<Real>(v, qp, &c)) {
+        q[g * L.nv + j] = (int32_t)(uint32_t)RawBits<Real>::to(v);
+        atomicOr(w, 1u << (j & 31));
+      } else {
+        q[g * L.nv + j] = c;
+        atomicAnd(w, ~(1u << (j & 31)));
+      }
+      return;
+    }
     if (quantize<Real>(v, qp, &c)) {
       const int i = atomicAdd(&vout_cnt[g], 1);
       if (i < kVmax) {
@@ -476,6 +529,74 @@ struct Worker {
   // Compress(S) for one block: q codes + verbatim list -> stream in the output arena.
   // ------------------------------------------------------------------------------------
   __device__ void encode(int g, unsigned long long blk, const PassArgs& a);
+
+  // complex64: write the verbatim section (u16 positions ascending, raw floats) of block g
+  // into its stream at `out`, after the zero fill of the section
+  __device__ void write_verbatim_inplace(int g, uint8_t* out, uint32_t body_end, int nverb) {
+    const int tid = threadIdx.x, nv = L.nv, j0 = tid * vpt;
+    const uint32_t w = vmask[g * (nv >> 5) + (j0 >> 5)];
+    const uint32_t mine = vpt >= 32 ? w : ((w >> (j0 & 31)) & ((1u << vpt) - 1u));
+    uint32_t tot = 0;
+    uint32_t k = block_excl_scan_u32((uint32_t)__popc(mine), m->scan, &tot);
+    const uint32_t valoff = (uint32_t)pad_to(body_end + 2 * nverb, sizeof(Real));
+    for (int i = 0; i < vpt; ++i) {
+      if (!((mine >> i) & 1u)) continue;
+      const int j = j0 + i;
+      *(uint16_t*)(out + body_end + 2 * k) = (uint16_t)j;
+      *(uint32_t*)(out + valoff + 4 * k) = (uint32_t)q[g * nv + j];
+      ++k;
+    }
+  }
+
+  // Pairwise sum of x*x over the block's values (x verbatim) and +0 (others), level by
+  // level: each thread reduces its aligned run of vpt values with a stack of partial sums
+  // (every node is fl(left + right)), then the runs are reduced across threads. All threads
+  // call it; the result is returned to all.
+  __device__ double verbatim_square_tree(int g) {
+    const int tid = threadIdx.x, nv = L.nv, j0 = tid * vpt;
+    double stk[7];
+    int lvl[7], top = 0;
+    for (int i = 0; i < vpt; ++i) {
+      const int j = j0 + i;
+      double x2 = 0.0;
+      if (kMask) {
+        if (is_verb(g, j)) {
+          const double x = (double)RawBits<Real>::from((uint32_t)q[g * nv + j]);
+          x2 = __dmul_rn(x, x);
+        }
+      } else {
+        const int n = vout_cnt[g] < kVmax ? vout_cnt[g] : kVmax;
+        for (int e = 0; e < n; ++e)
+          if (vout_pos[g * kVmax + e] == j) {
+            const double x = (double)RawBits<Real>::from(vout_bits[g * kVmax + e]);
+            x2 = __dmul_rn(x, x);
+          }
+      }
+      double v = x2;
+      int l = 0;
+      while (top > 0 && lvl[top - 1] == l) {
+        v = __dadd_rn(stk[top - 1], v);
+        --top;
+        ++l;
+      }
+      stk[top] = v;
+      lvl[top] = l;
+      ++top;
+    }
+    vtree[tid] = stk[0];
+    __syncthreads();
+    for (int cnt = T; cnt > 1; cnt >>= 1) {
+      const int half = cnt >> 1;
+      double v = 0.0;
+      if (tid < half) v = __dadd_rn(vtree[2 * tid], vtree[2 * tid + 1]);
+      __syncthreads();
+      if (tid < half) vtree[tid] = v;
+      __syncthreads();
+    }
+    const double r = vtree[0];
+    __syncthreads();
+    return r;
+  }
 };
 
 // Two-queue Huffman merge over D >= 2 leaves sorted by (frequency, symbol) in keys (frequency
@@ -572,13 +693,19 @@ template <typename Real>
 __device__ void Worker<Real>::encode(int g, unsigned long long blk, const PassArgs& a) {
   const int tid = threadIdx.x, nv = L.nv;
   const int32_t* qb = q + g * nv;
-  const int nverb_raw = vout_cnt[g];
-  const int nverb = nverb_raw < kVmax ? nverb_raw : kVmax;
+  int nverb_raw, nverb;
+  if (kMask) {  // verbatim values flagged in place: count the flags
+    const unsigned long long c1 = tid < (nv >> 5) ? (unsigned long long)__popc(vmask[g * (nv >> 5) + tid]) : 0ull;
+    nverb_raw = nverb = (int)block_reduce_sum_u64(c1, m->red);
+  } else {
+    nverb_raw = vout_cnt[g];
+    nverb = nverb_raw < kVmax ? nverb_raw : kVmax;
+  }
   const int C = nv / kChunk;
   // ---- pass 1: statistics over this thread's values ----
   const int j0 = tid * vpt;
   const int32_t q0 = qb[0], q1 = qb[1];
-  int32_t pr = j0 >= 2 ? qb[j0 - 2] : 0, pi = j0 >= 2 ? qb[j0 - 1] : 0;
+  int32_t pr = j0 >= 2 ? code(g, j0 - 2) : 0, pi = j0 >= 2 ? code(g, j0 - 1) : 0;
   unsigned long long sqh = 0, sql = 0;
   uint32_t zmax = 0;
   int nesc = 0;
@@ -586,7 +713,7 @@ __device__ void Worker<Real>::encode(int g, unsigned long long blk, const PassAr
 #pragma unroll 4
   for (int i = 0; i < vpt; ++i) {
     const int j = j0 + i;
-    const int32_t c = qb[j];
+    const int32_t c = code(g, j);
     const int32_t p = (j & 1) ? pi : pr;
     const int32_t d = c - p;
     if (j & 1) pi = c;
@@ -629,13 +756,13 @@ __device__ void Worker<Real>::encode(int g, unsigned long long blk, const PassAr
     __syncthreads();
     atomicAdd(&m->nesc, nesc);
     {
-      int32_t pr2 = j0 >= 2 ? qb[j0 - 2] : 0, pi2 = j0 >= 2 ? qb[j0 - 1] : 0;
+      int32_t pr2 = j0 >= 2 ? code(g, j0 - 2) : 0, pi2 = j0 >= 2 ? code(g, j0 - 1) : 0;
       uint32_t run_sym = 0xFFFFFFFFu, run = 0;
       for (int i = 0; i <= vpt; ++i) {
         uint32_t sym = 0xFFFFFFFEu;
         if (i < vpt) {
           const int j = j0 + i;
-          const int32_t c = qb[j];
+          const int32_t c = code(g, j);
           const int32_t d = c - ((j & 1) ? pi2 : pr2);
           if (j & 1) pi2 = c;
           else pr2 = c;
@@ -761,8 +888,11 @@ __device__ void Worker<Real>::encode(int g, unsigned long long blk, const PassAr
   }
   __syncthreads();
   const bool ok = m->ok;
+  // complex64: the stream image in shared memory ends with the body; the verbatim section is
+  // written straight to the output (it can be as large as the whole block)
+  const uint32_t span = (kMask && mode != kModeConst) ? (uint32_t)pad_to(body_end, 16) : size;
   if (ok) {
-    for (uint32_t i = tid; i < size / 4; i += T) stage[i] = 0;
+    for (uint32_t i = tid; i < span / 4; i += T) stage[i] = 0;
     __syncthreads();
     if (tid == 0) {
       const int want_dt = sizeof(Real) == 8 ? 2 : 1;
@@ -789,10 +919,10 @@ __device__ void Worker<Real>::encode(int g, unsigned long long blk, const PassAr
         // pass 2: bits per thread, then positions
         uint32_t nb = 0;
         {
-          int32_t pr2 = j0 >= 2 ? qb[j0 - 2] : 0, pi2 = j0 >= 2 ? qb[j0 - 1] : 0;
+          int32_t pr2 = j0 >= 2 ? code(g, j0 - 2) : 0, pi2 = j0 >= 2 ? code(g, j0 - 1) : 0;
           for (int i = 0; i < vpt; ++i) {
             const int j = j0 + i;
-            const int32_t c = qb[j];
+            const int32_t c = code(g, j);
             const int32_t d = c - ((j & 1) ? pi2 : pr2);
             if (j & 1) pi2 = c;
             else pr2 = c;
@@ -816,10 +946,10 @@ __device__ void Worker<Real>::encode(int g, unsigned long long blk, const PassAr
         BitWriter bw;
         bw.start(pay, start);
         {
-          int32_t pr2 = j0 >= 2 ? qb[j0 - 2] : 0, pi2 = j0 >= 2 ? qb[j0 - 1] : 0;
+          int32_t pr2 = j0 >= 2 ? code(g, j0 - 2) : 0, pi2 = j0 >= 2 ? code(g, j0 - 1) : 0;
           for (int i = 0; i < vpt; ++i) {
             const int j = j0 + i;
-            const int32_t c = qb[j];
+            const int32_t c = code(g, j);
             const int32_t d = c - ((j & 1) ? pi2 : pr2);
             if (j & 1) pi2 = c;
             else pr2 = c;
@@ -835,10 +965,10 @@ __device__ void Worker<Real>::encode(int g, unsigned long long blk, const PassAr
         pay = stage + kHdr / 4;
         BitWriter bw;
         bw.start(pay, (uint32_t)(j0 * width));
-        int32_t pr2 = j0 >= 2 ? qb[j0 - 2] : 0, pi2 = j0 >= 2 ? qb[j0 - 1] : 0;
+        int32_t pr2 = j0 >= 2 ? code(g, j0 - 2) : 0, pi2 = j0 >= 2 ? code(g, j0 - 1) : 0;
         for (int i = 0; i < vpt; ++i) {
           const int j = j0 + i;
-          const int32_t c = qb[j];
+          const int32_t c = code(g, j);
           const int32_t d = c - ((j & 1) ? pi2 : pr2);
           if (j & 1) pi2 = c;
           else pr2 = c;
@@ -847,7 +977,7 @@ __device__ void Worker<Real>::encode(int g, unsigned long long blk, const PassAr
         bw.finish();
       }
       // verbatim section (positions ascending)
-      if (nverb > 0) {
+      if (!kMask && nverb > 0) {
         __syncthreads();
         if (tid == 0) {
           // insertion sort of the (rare) verbatim list by position
@@ -878,7 +1008,12 @@ __device__ void Worker<Real>::encode(int g, unsigned long long blk, const PassAr
     __syncthreads();
     uint4* dst = (uint4*)(a.out_arena + m->out_off);
     const uint4* src = (const uint4*)stage;
-    for (uint32_t i = tid; i < size / 16; i += T) dst[i] = src[i];
+    for (uint32_t i = tid; i < span / 16; i += T) dst[i] = src[i];
+    if (kMask && mode != kModeConst && nverb > 0) {
+      for (uint32_t i = span / 16 + tid; i < size / 16; i += T) dst[i] = make_uint4(0u, 0u, 0u, 0u);
+      __syncthreads();  // the zero fill lands before the positions and values below
+      write_verbatim_inplace(g, a.out_arena + m->out_off, body_end, nverb);
+    }
     if (tid == 0) {
       a.out_off[blk] = m->out_off;
       a.out_len[blk] = size;
@@ -893,17 +1028,12 @@ __device__ void Worker<Real>::encode(int g, unsigned long long blk, const PassAr
     const unsigned long long old = atomicAdd(&a.sc->acc.sq_lo, lo);
     const unsigned long long c1 = (old + lo < old) ? 1ull : 0ull;
     if (hi + c1) atomicAdd(&a.sc->acc.sq_hi, hi + c1);
-    double v = 0.0;
-    const uint64_t* vb = vout_bits + g * kVmax;
-    for (int i = 0; i < nverb; ++i) {
-      const double x = (double)RawBits<Real>::from(vb[i]);
-      v = __dadd_rn(v, __dmul_rn(x, x));
-    }
-    if (a.vsum) a.vsum[blk] = v;
     if (nverb) atomicAdd(&a.sc->acc.n_verbatim, (unsigned long long)nverb);
     if (mode != kModeConst) atomicAdd(&a.sc->acc.n_escape, (unsigned long long)m->nesc);
     atomicAdd(&a.sc->acc.modes[mode], 1ull);
   }
+  const double vs = nverb > 0 ? verbatim_square_tree(g) : 0.0;
+  if (tid == 0 && a.vsum) a.vsum[blk] = vs;
   __syncthreads();
 }
 

@@ -620,6 +620,7 @@ __global__ void __launch_bounds__(256) k_codec_compress(const Real* values, Pass
   for (unsigned long long blk = blockIdx.x; blk < a.ngroups; blk += gridDim.x) {
     __syncthreads();
     if (threadIdx.x == 0) w.vout_cnt[0] = 0;
+    for (int i = threadIdx.x; i < (L.nv >> 5); i += blockDim.x) w.vmask[i] = 0u;
     __syncthreads();
     const Real* v = values + blk * (unsigned long long)L.nv;
     for (int j = threadIdx.x; j < L.nv; j += blockDim.x) w.put_value(0, j, v[j]);

@@ -1,0 +1,150 @@
+"""Continuous-batching request loop over compressed state vectors.
+
+Requests (circuit simulations of uneven size, dtype and error bound) arrive over time; each is
+admitted when its estimated pool footprint fits the budget, gets a compressed state on the
+device, and from then on advances by one gate per step, batched with every other active
+request of the same (dtype, block size) in one fused pass launch (sv_batch_apply, optionally
+replayed from CUDA graphs). Requests that finish leave the batch and free their memory;
+waiting ones are admitted as room appears. The loop records each request's latency
+(completion - arrival) and the served amplitude-updates.
+"""
+from __future__ import annotations
+
+import collections
+import time
+from dataclasses import dataclass, field
+from typing import Dict, List, Optional
+
+import numpy as np
+import torch
+
+from . import sv
+from .circuits import Request
+
+
+@dataclass
+class Result:
+    rid: int
+    arrival: float
+    admitted: float
+    done: float
+    amp_updates: int
+    streams: Optional[List[bytes]] = None
+    norm: Optional[float] = None
+
+    @property
+    def latency(self) -> float:
+        return self.done - self.arrival
+
+
+def footprint(req: Request, block_log2: int) -> int:
+    """Pool bytes reserved at admission: metadata plus two arenas sized for a 2x compressed
+    state (arenas grow on overflow while the request runs)."""
+    raw = (16 if req.dtype == 2 else 8) << req.n
+    nb = 1 << (req.n - block_log2)
+    return raw + 48 * nb + (8 << 20)
+
+
+class Server:
+    def __init__(self, pool_bytes: int, budget_bytes: int, block_log2: int = 10, max_batch: int = 64,
+                 graphs: bool = True, keep_results: bool = False):
+        self.pool = sv.Pool(pool_bytes)
+        self.budget = budget_bytes
+        self.block_log2 = block_log2
+        self.max_batch = max_batch
+        self.graphs = graphs
+        self.keep = keep_results
+        self.streams: Dict[tuple, torch.cuda.Stream] = {}
+        self.batches: Dict[tuple, sv.Batch] = {}
+
+    def _bucket(self, req: Request):
+        key = (req.dtype, min(self.block_log2, req.n))
+        if key not in self.batches:
+            self.streams[key] = torch.cuda.Stream()
+            self.batches[key] = sv.Batch(self.pool, self.max_batch, stream=self.streams[key], graphs=self.graphs)
+        return key
+
+    def run(self, requests: List[Request], time_limit: Optional[float] = None) -> dict:
+        pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
+        waiting: collections.deque = collections.deque()
+        active: Dict[tuple, list] = collections.defaultdict(list)  # key -> [req, state, next gate, t_admit]
+        used = 0
+        results: List[Result] = []
+        served = 0
+        steps = 0
+        t0 = time.time()
+        while pending or waiting or any(active.values()):
+            now = time.time() - t0
+            if time_limit is not None and now > time_limit:
+                break
+            while pending and pending[0].arrival <= now:
+                waiting.append(pending.popleft())
+            # admission in arrival order while the footprint fits the budget
+            while waiting:
+                req = waiting[0]
+                fp = footprint(req, min(self.block_log2, req.n))
+                key = (req.dtype, min(self.block_log2, req.n))
+                if used + fp > self.budget or len(active[key]) >= self.max_batch:
+                    break
+                waiting.popleft()
+                key = self._bucket(req)
+                st = sv.State(self.pool, req.n, req.n, req.eb, req.dtype, block_log2=key[1],
+                              stream=self.streams[key])
+                st.reset_basis(req.basis)
+                used += fp
+                active[key].append([req, st, 0, now, fp])
+            if not any(active.values()):
+                if pending:
+                    time.sleep(max(0.0, min(pending[0].arrival - (time.time() - t0), 0.05)))
+                continue
+            # one step: every active request advances by one gate (one launch per bucket)
+            for key, lst in active.items():
+                if lst:
+                    self.batches[key].apply([e[1] for e in lst], [e[0].gates[e[2]] for e in lst])
+                    for e in lst:
+                        e[2] += 1
+                        served += 1 << e[0].n
+            steps += 1
+            for key, lst in active.items():
+                if not any(e[2] == len(e[0].gates) for e in lst):
+                    continue
+                self.streams[key].synchronize()
+                tdone = time.time() - t0
+                keep = []
+                for e in lst:
+                    req, st, nxt, tadm, fp = e
+                    if nxt < len(req.gates):
+                        keep.append(e)
+                        continue
+                    st.sync()
+                    res = Result(req.rid, req.arrival, tadm, tdone, req.amp_updates)
+                    if self.keep:
+                        nb = 1 << (req.n - key[1])
+                        res.streams = [st.block_stream(i) for i in range(nb)]
+                        res.norm = st.norm()
+                    st.close()
+                    used -= fp
+                    results.append(res)
+                lst[:] = keep
+        wall = time.time() - t0
+        for lst in active.values():
+            for e in lst:
+                e[1].close()
+        lat = np.array([r.latency for r in results]) if results else np.zeros(0)
+        offered = sum(r.amp_updates for r in requests)
+        span = max((r.arrival for r in requests), default=0.0)
+        return {
+            "requests": len(requests), "completed": len(results), "waiting_at_end": len(waiting) + len(pending),
+            "active_at_end": sum(len(v) for v in active.values()), "steps": steps, "wall_s": wall,
+            "p50_s": float(np.percentile(lat, 50)) if lat.size else None,
+            "p99_s": float(np.percentile(lat, 99)) if lat.size else None,
+            "served_amp_updates_per_s": served / wall if wall > 0 else 0.0,
+            "offered_amp_updates_per_s": offered / span if span > 0 else None,
+            "results": results,
+        }
+
+    def close(self):
+        for b in self.batches.values():
+            b.close()
+        self.batches.clear()
+        self.pool.close()

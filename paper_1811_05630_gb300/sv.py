@@ -274,8 +274,8 @@ def codec_compress(values: torch.Tensor, block_log2: int, error_bound: float, ca
     B = 1 << block_log2
     nblocks = values.numel() // B
     assert nblocks * B == values.numel()
-    if cap is None:
-        cap = nblocks * (16 + 4 * 2 * B + 2 * 128 + 8 + 128 * 8 + 32)
+    if cap is None:  # largest stream: PACK at 32 bits plus every value verbatim
+        cap = nblocks * (16 + 4 * 2 * B + 2 * 2 * B + 8 * 2 * B + 32)
     out = torch.zeros(cap, dtype=torch.uint8, device=values.device)
     offs = torch.zeros(nblocks, dtype=torch.int64, device=values.device)
     lens = torch.zeros(nblocks, dtype=torch.int32, device=values.device)

@@ -98,6 +98,15 @@ def test_random_brickwork_bit_exact(sv, pool, dtype, eb):
     run_compare(sv, pool, n, 9, 6, dtype, eb, 0, C.random_brickwork(n, 4, seed=21), every=5)
 
 
+def test_complex64_fine_bound_verbatim_heavy(sv, pool):
+    # complex64 at eb 1e-8: the float grid is about as coarse as the quantization grid, so
+    # many values are stored verbatim in place; every pass must still match the oracle
+    n = 10
+    gates = C.qft(n)[:30] + C.random_brickwork(n, 2, seed=6)
+    stats, _ = run_compare(sv, pool, n, 9, 7, oracle.C64, 1e-8, C.seeded_index(4, n), gates, every=3)
+    assert stats["n_verbatim"] > 0
+
+
 def test_grover_bit_exact_and_success_probability(sv, pool):
     n, eb = 10, 1e-8
     marked = C.seeded_index(2, n)
