@@ -409,6 +409,39 @@ def run_full_circuit(args):
     return res
 
 
+def run_serving(args):
+    """The mixed request stream (2000 Poisson requests at 20/s by default) through the
+    continuous-batching loop for --serve-seconds of wall time."""
+    from paper_1811_05630_gb300.serve import Server, size_class
+
+    reqs = C.serving_requests(count=args.serve_count, rate=args.serve_rate, seed=0)
+    srv = Server(pool_bytes=int(args.pool_gb * (1 << 30)), budget_bytes=int(args.serve_budget_gb * 1e9),
+                 block_log2=10, max_batch=64, graphs=True)
+    with ClockSampler(0) as clk:
+        out = srv.run(reqs, time_limit=args.serve_seconds)
+    res = out.pop("results")
+    out["failed_requests"] = [{"rid": r.rid, "kind": reqs[r.rid].kind, "n": reqs[r.rid].n,
+                               "dtype": reqs[r.rid].dtype, "eb": reqs[r.rid].eb, "error": r.error}
+                              for r in res if r.error]
+    by = {}
+    for r in res:
+        if r.error:
+            continue
+        c = size_class(reqs[r.rid].n)
+        by.setdefault(c, []).append(r.latency)
+    out["completed_by_size_class"] = {["n<=16", "17-22", "23-28"][c]: len(v) for c, v in sorted(by.items())}
+    out["p50_s_by_size_class"] = {["n<=16", "17-22", "23-28"][c]: float(np.percentile(v, 50)) for c, v in sorted(by.items())}
+    out["p99_s_by_size_class"] = {["n<=16", "17-22", "23-28"][c]: float(np.percentile(v, 99)) for c, v in sorted(by.items())}
+    arrived = sum(1 for r in reqs if r.arrival <= out["wall_s"])
+    out["arrived_within_limit"] = arrived
+    out["offered_within_limit_amp_updates_per_s"] = sum(r.amp_updates for r in reqs if r.arrival <= out["wall_s"]) / out["wall_s"]
+    out["config"] = {"requests": args.serve_count, "rate_per_s": args.serve_rate, "budget_gb": args.serve_budget_gb,
+                     "time_limit_s": args.serve_seconds, "block_log2": 10, "max_batch": 64, "graphs": True}
+    out["clocks"] = clk.summary()
+    srv.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -424,9 +457,17 @@ def main():
     ap.add_argument("--no-fidelity", dest="fidelity", action="store_false")
     ap.add_argument("--full-circuit", action="store_true",
                     help="run the whole circuit once (per-gate sizes, closed-form fidelity)")
+    ap.add_argument("--serve", action="store_true", help="serve the mixed request stream")
+    ap.add_argument("--serve-count", type=int, default=2000)
+    ap.add_argument("--serve-rate", type=float, default=20.0)
+    ap.add_argument("--serve-seconds", type=float, default=90.0)
+    ap.add_argument("--serve-budget-gb", type=float, default=120.0)
     args = ap.parse_args()
     if args.full_circuit:
         print(json.dumps(run_full_circuit(args)))
+        return
+    if args.serve:
+        print(json.dumps(run_serving(args)))
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -137,6 +137,9 @@ typedef struct sv_batch sv_batch;
 int sv_batch_create(sv_pool* pool, int max_states, void* stream, sv_batch** out);
 int sv_batch_destroy(sv_batch* batch);
 int sv_batch_use_graphs(sv_batch* batch, int on);
+/* 1 when sv_batch_apply would not wait for the host staging buffer of an earlier step
+ * (lets a host loop serve other batches meanwhile), 0 otherwise, <0 on error. */
+int sv_batch_ready(sv_batch* batch);
 int sv_batch_apply(sv_batch* batch, sv_state* const* states, const sv_gate_t* gates, int count);
 
 /* Wait for the state's stream, resolve arena overflow (grow + replay) and return any

@@ -279,11 +279,19 @@ int launch_logged(sv_state* s, const Logged& lg) {
   return cuda_err(e);
 }
 
-// Record one step in a state's log (after its launch) and flip its arenas.
+// Record one step in a state's log (after its launch) and flip its arenas. Every 256 steps
+// the state is checked (and an overflow replayed); an error that cannot be recovered (a
+// collapsed norm, a corrupt stream) stays with the state — its own sv_sync reports it — and
+// the state is no longer logged, so a batch carrying it goes on for the others.
 int log_step(sv_state* s, Logged&& lg) {
   s->cur ^= 1;
+  if (s->sticky_err) return SV_OK;
   s->log.push_back(std::move(lg));
-  if (s->log.size() >= 256) return sv_sync(s);
+  if (s->log.size() >= 256) {
+    const int rc = sv_sync(s);
+    if (rc == SV_ERR_CUDA) return rc;
+    if (rc) s->sticky_err = rc;
+  }
   return SV_OK;
 }
 
@@ -293,10 +301,8 @@ int submit(sv_state* s, Logged lg) {
   lg.out_id = s->cur ^ 1;
   int rc = launch_logged(s, lg);
   if (rc) return rc;
-  s->cur ^= 1;
-  s->log.push_back(std::move(lg));
-  if (s->log.size() >= 256) return sv_sync(s);
-  return SV_OK;
+  rc = log_step(s, std::move(lg));
+  return rc ? rc : s->sticky_err;
 }
 
 int read_scalars(sv_state* s, DevScalars* h) {
@@ -860,6 +866,14 @@ int sv_batch_destroy(sv_batch* bt) {
   }
   delete bt;
   return SV_OK;
+}
+
+int sv_batch_ready(sv_batch* bt) {
+  if (!bt) return SV_ERR_ARG;
+  const cudaError_t e = cudaEventQuery(bt->h_done[bt->ring]);
+  if (e == cudaSuccess) return 1;
+  if (e == cudaErrorNotReady) return 0;
+  return cuda_err(e);
 }
 
 int sv_batch_use_graphs(sv_batch* bt, int on) {

@@ -31,6 +31,7 @@ class Result:
     amp_updates: int
     streams: Optional[List[bytes]] = None
     norm: Optional[float] = None
+    error: Optional[str] = None  # e.g. SV_ERR_NORM: every amplitude quantized to zero
 
     @property
     def latency(self) -> float:
@@ -45,6 +46,11 @@ def footprint(req: Request, block_log2: int) -> int:
     return raw + 48 * nb + (8 << 20)
 
 
+def size_class(n: int) -> int:
+    """Requests of similar size share a batch (a step lasts as long as its largest pass)."""
+    return 0 if n <= 16 else (1 if n <= 22 else 2)
+
+
 class Server:
     def __init__(self, pool_bytes: int, budget_bytes: int, block_log2: int = 10, max_batch: int = 64,
                  graphs: bool = True, keep_results: bool = False):
@@ -57,85 +63,102 @@ class Server:
         self.streams: Dict[tuple, torch.cuda.Stream] = {}
         self.batches: Dict[tuple, sv.Batch] = {}
 
-    def _bucket(self, req: Request):
-        key = (req.dtype, min(self.block_log2, req.n))
+    def key(self, req: Request) -> tuple:
+        return (req.dtype, min(self.block_log2, req.n), size_class(req.n))
+
+    def _bucket(self, key: tuple):
         if key not in self.batches:
             self.streams[key] = torch.cuda.Stream()
             self.batches[key] = sv.Batch(self.pool, self.max_batch, stream=self.streams[key], graphs=self.graphs)
-        return key
 
     def run(self, requests: List[Request], time_limit: Optional[float] = None) -> dict:
+        """Serve `requests` (arrival times relative to the start of this call). Each bucket
+        steps on its own stream whenever its staging ring has room, so small requests are not
+        held to the pace of large ones; completions are seen through CUDA events."""
         pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
         waiting: collections.deque = collections.deque()
-        active: Dict[tuple, list] = collections.defaultdict(list)  # key -> [req, state, next gate, t_admit]
+        active: Dict[tuple, list] = collections.defaultdict(list)  # key -> [req, state, next, t_admit, fp]
+        finishing: list = []  # [req, state, event, t_admit, fp, key]
         used = 0
         results: List[Result] = []
         served = 0
         steps = 0
         t0 = time.time()
-        while pending or waiting or any(active.values()):
+        while pending or waiting or finishing or any(active.values()):
             now = time.time() - t0
             if time_limit is not None and now > time_limit:
                 break
             while pending and pending[0].arrival <= now:
                 waiting.append(pending.popleft())
-            # admission in arrival order while the footprint fits the budget
-            while waiting:
+            while waiting:  # admission in arrival order while the footprint fits
                 req = waiting[0]
-                fp = footprint(req, min(self.block_log2, req.n))
-                key = (req.dtype, min(self.block_log2, req.n))
+                key = self.key(req)
+                fp = footprint(req, key[1])
                 if used + fp > self.budget or len(active[key]) >= self.max_batch:
                     break
                 waiting.popleft()
-                key = self._bucket(req)
+                self._bucket(key)
                 st = sv.State(self.pool, req.n, req.n, req.eb, req.dtype, block_log2=key[1],
                               stream=self.streams[key])
                 st.reset_basis(req.basis)
                 used += fp
                 active[key].append([req, st, 0, now, fp])
-            if not any(active.values()):
-                if pending:
-                    time.sleep(max(0.0, min(pending[0].arrival - (time.time() - t0), 0.05)))
-                continue
-            # one step: every active request advances by one gate (one launch per bucket)
+            progressed = False
             for key, lst in active.items():
-                if lst:
-                    self.batches[key].apply([e[1] for e in lst], [e[0].gates[e[2]] for e in lst])
-                    for e in lst:
-                        e[2] += 1
-                        served += 1 << e[0].n
-            steps += 1
-            for key, lst in active.items():
-                if not any(e[2] == len(e[0].gates) for e in lst):
+                if not lst or not self.batches[key].ready():
                     continue
-                self.streams[key].synchronize()
-                tdone = time.time() - t0
+                self.batches[key].apply([e[1] for e in lst], [e[0].gates[e[2]] for e in lst])
+                progressed = True
+                steps += 1
                 keep = []
                 for e in lst:
-                    req, st, nxt, tadm, fp = e
-                    if nxt < len(req.gates):
+                    e[2] += 1
+                    served += 1 << e[0].n
+                    if e[2] == len(e[0].gates):
+                        ev = torch.cuda.Event()
+                        ev.record(self.streams[key])
+                        finishing.append([e[0], e[1], ev, e[3], e[4], key])
+                    else:
                         keep.append(e)
-                        continue
-                    st.sync()
-                    res = Result(req.rid, req.arrival, tadm, tdone, req.amp_updates)
-                    if self.keep:
-                        nb = 1 << (req.n - key[1])
-                        res.streams = [st.block_stream(i) for i in range(nb)]
-                        res.norm = st.norm()
-                    st.close()
-                    used -= fp
-                    results.append(res)
                 lst[:] = keep
+            still = []
+            for f in finishing:
+                req, st, ev, tadm, fp, key = f
+                if not ev.query():
+                    still.append(f)
+                    continue
+                tdone = time.time() - t0
+                res = Result(req.rid, req.arrival, tadm, tdone, req.amp_updates)
+                try:
+                    st.sync()
+                except sv.SvError as ex:
+                    res.error = str(ex)
+                if self.keep and res.error is None:
+                    res.streams = [st.block_stream(i) for i in range(1 << (req.n - key[1]))]
+                    res.norm = st.norm()
+                st.close()
+                used -= fp
+                results.append(res)
+                progressed = True
+            finishing = still
+            if not progressed:
+                time.sleep(0.0002)
         wall = time.time() - t0
         for lst in active.values():
             for e in lst:
                 e[1].close()
-        lat = np.array([r.latency for r in results]) if results else np.zeros(0)
+        for f in finishing:
+            f[1].close()
+        ok = [r for r in results if r.error is None]
+        lat = np.array([r.latency for r in ok]) if ok else np.zeros(0)
         offered = sum(r.amp_updates for r in requests)
         span = max((r.arrival for r in requests), default=0.0)
         return {
-            "requests": len(requests), "completed": len(results), "waiting_at_end": len(waiting) + len(pending),
-            "active_at_end": sum(len(v) for v in active.values()), "steps": steps, "wall_s": wall,
+            "requests": len(requests), "completed": len(ok), "failed": len(results) - len(ok),
+            "failure_reasons": sorted({r.error for r in results if r.error}),
+            "waiting_at_end": len(waiting) + len(pending),
+            "active_at_end": sum(len(v) for v in active.values()) + len(finishing),
+            "steps": steps, "wall_s": wall,
             "p50_s": float(np.percentile(lat, 50)) if lat.size else None,
             "p99_s": float(np.percentile(lat, 99)) if lat.size else None,
             "served_amp_updates_per_s": served / wall if wall > 0 else 0.0,

@@ -84,6 +84,7 @@ _SIGS = {
     "sv_batch_create": ([_vp, _i, _vp, _P(_vp)], _i),
     "sv_batch_destroy": ([_vp], _i),
     "sv_batch_use_graphs": ([_vp, _i], _i),
+    "sv_batch_ready": ([_vp], _i),
     "sv_batch_apply": ([_vp, _vp, _vp, _i], _i),
     "sv_set_pass_timing": ([_vp, _i], _i),
     "sv_get_pass_timing": ([_vp, _P(_d), _P(_u64), _P(_u64)], _i),
@@ -241,6 +242,12 @@ class Batch:
 
     def use_graphs(self, on: bool):
         _check(_L.sv_batch_use_graphs(self._h, 1 if on else 0), "sv_batch_use_graphs")
+
+    def ready(self) -> bool:
+        r = _L.sv_batch_ready(self._h)
+        if r < 0:
+            _check(r, "sv_batch_ready")
+        return r == 1
 
     def apply(self, states, gates):
         n = len(states)
