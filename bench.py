@@ -193,17 +193,38 @@ def run_ours(args, rank, world, dist):
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
     wl = workload(args.workload)
-    if args.block_log2:
-        wl["block_log2"] = args.block_log2
     n = wl["n"]
     gates = wl["gates"]
+    tuned = None
+    if args.block_log2:
+        wl["block_log2"] = args.block_log2
+    elif args.autotune and n <= 30:
+        from paper_1811_05630_gb300 import tune
+
+        i0t = start_of_dense_stage(wl)
+        tuned = tune.best_config(n, wl["dtype"], wl["eb"], wl["name"], gates[:i0t], gates[i0t:i0t + 200],
+                                 basis=wl["basis"], use_cache=False)
+        wl["block_log2"] = tuned["block_log2"]
+        wl["threads"] = tuned["threads"]
     i0 = start_of_dense_stage(wl)
     need = args.warmup + args.steps
     assert i0 + need <= len(gates), "not enough gates for the requested steps"
+    if args.threads:
+        wl["threads"] = args.threads
     pool_bytes = int(args.pool_gb * (1 << 30))
     pool = sv.Pool(pool_bytes)
+    arena = args.arena_mb << 20
+    if not arena:
+        # arenas sized for the largest possible streams (every block PACK at 32 bits plus its
+        # verbatim section) when that is small, so no pass can overflow and be replayed
+        nv = 2 << wl["block_log2"]
+        verb = 10 * min(nv, 128) if wl["dtype"] == 2 else 6 * nv
+        worst = (1 << (n - wl["block_log2"])) * (16 + 4 * nv + verb + 32)
+        arena = worst if worst <= (512 << 20) else 0
     st = sv.State(pool, n, wl["slice_log2"], wl["eb"], wl["dtype"], block_log2=wl["block_log2"],
-                  arena_bytes=args.arena_mb << 20)
+                  arena_bytes=arena)
+    if wl.get("threads"):
+        st.set_threads(wl["threads"])
     st.reset_basis(wl["basis"])
     st.run(gates[:i0])
     for g in gates[i0:i0 + args.warmup]:
@@ -213,19 +234,26 @@ def run_ours(args, rank, world, dist):
     st.set_pass_timing(True)
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # L2 (126 MiB) is flushed between timed steps by writing a 512 MiB buffer on the same
+    # stream; each step is bracketed by its own events, so the flush is not timed
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in timed]
+    replays0 = st.stats()["replayed_passes"]
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(dev) as clk:
-        e0.record(stream)
-        for g in timed:
+        for i, g in enumerate(timed):
+            flush.fill_(i & 0xFF)
+            ev[i][0].record(stream)
             st.apply(g.matrix, g.targets, g.controls)
-        e1.record(stream)
+            ev[i][1].record(stream)
         st.sync()
         torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
+    ms = sum(a.elapsed_time(b) for a, b in ev)
     kern_ms, npass, alg_bytes = st.pass_timing()
     stats = st.stats()
+    replays = stats["replayed_passes"] - replays0
     if dist:
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -239,9 +267,12 @@ def run_ours(args, rank, world, dist):
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    t = time.time()
+    e2e_s = 0.0
     h2d = d2h = 0
-    for g in e2e_gates:
+    for i, g in enumerate(e2e_gates):
+        flush.fill_(i & 0xFF)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
         gm = np.ascontiguousarray(g.matrix, dtype=np.complex128)
         pin_view = pin.numpy()[: gm.nbytes]
         pin_view[:] = gm.view(np.uint8).reshape(-1)
@@ -249,7 +280,8 @@ def run_ours(args, rank, world, dist):
         h2d += gm.nbytes + 4 * (len(g.targets) + len(g.controls))
         st.norm()
         d2h += 8
-    e2e_s = time.time() - t
+        e2e_s += time.perf_counter() - t
+    del flush
     e2e = {"value": (1 << n) * len(e2e_gates) * world / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": h2d // len(e2e_gates), "d2h_bytes_per_step": d2h // len(e2e_gates)}
 
@@ -276,12 +308,16 @@ def run_ours(args, rank, world, dist):
                 ps.reset_basis(wl["basis"])
                 ps.run(gates[:i0 + args.warmup])
                 ps.sync()
+                flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
                 torch.cuda.synchronize()
-                e0.record(stream)
-                ps.run(timed)
-                e1.record(stream)
+                for i, g in enumerate(timed):
+                    flush.fill_(i & 0xFF)
+                    ev[i][0].record(stream)
+                    ps.apply(g.matrix, g.targets, g.controls)
+                    ev[i][1].record(stream)
                 torch.cuda.synchronize()
-                pms = e0.elapsed_time(e1)
+                pms = sum(a.elapsed_time(b) for a, b in ev)
+                del flush
                 plain = (1 << n) * len(timed) / (pms * 1e-3)
                 ps.close()
                 ppool.close()
@@ -297,8 +333,11 @@ def run_ours(args, rank, world, dist):
             "warmup": args.warmup, "ms_per_step": ms / len(timed), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if wl["dtype"] == 2 else "f32",
             "data": "synthetic",
-            "config": {"workload": wl["desc"], "block_log2": wl["block_log2"], "parallelism": "replicas",
-                       "l2": "state streams read and written once per step; no flush (compressed state %d B)"
+            "config": {"workload": wl["desc"], "block_log2": wl["block_log2"],
+                       "threads_per_cta": wl.get("threads") or "default", "autotune": tuned,
+                       "arena_bytes": arena, "replayed_passes_in_timed_region": replays,
+                       "parallelism": "replicas",
+                       "l2": "flushed between timed steps (512 MiB write, untimed); compressed state %d B"
                              % stats["compressed_bytes"],
                        "compressed_bytes": stats["compressed_bytes"],
                        "compression_ratio": (16 << n) / max(1, stats["compressed_bytes"]),
@@ -450,6 +489,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="grover20", choices=["grover20", "qft34", "qft12", "random30"])
     ap.add_argument("--block-log2", type=int, default=0)
+    ap.add_argument("--threads", type=int, default=0, help="CTA size of the fused pass (0: tuned/default)")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="use the workload's fixed block size instead of tuning it")
     ap.add_argument("--pool-gb", type=float, default=8.0)
     ap.add_argument("--arena-mb", type=int, default=0)
     ap.add_argument("--cpu-budget", type=float, default=15.0)

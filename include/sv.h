@@ -68,6 +68,10 @@ typedef struct {
   uint64_t n_verbatim, n_escape;
   double norm;               /* N of the stored state after the pass */
   double sigma;              /* scale the next pass applies, 1/sqrt(norm) */
+  uint64_t blocks_reused;    /* blocks whose stream the pass re-emitted unchanged: the pass
+                                provably reproduced their codes (or a partner block's), so
+                                the stream is what recoding would have written */
+  uint64_t replayed_passes;  /* passes re-run after an arena overflow, since creation */
 } sv_stats_t;
 
 /* ---------------------------------------------------------------------------------------
@@ -165,6 +169,13 @@ int sv_read_amplitudes(sv_state* s, uint64_t start, uint64_t count, double* out)
 int sv_fidelity(sv_state* a, sv_state* b, double* out);
 int sv_compressed_bytes(sv_state* s, uint64_t* out);
 int sv_stats(sv_state* s, sv_stats_t* out);
+
+/* Threads per CTA of the fused pass for this state (an autotuning knob; the paper has no
+ * counterpart): 0 restores the default (one thread per 32-value decode chunk, 32..256);
+ * otherwise a power of two T, 32 <= T <= 256, with 2 <= 2^(block_log2+1) / T <= 32.
+ * Results (streams, norms) do not depend on it. SV_ERR_ARG for other values or a plain
+ * state. A batch runs with the setting of its first state. */
+int sv_set_threads(sv_state* s, int threads);
 int sv_norm(sv_state* s, double* out);
 
 /* Overlap with the exact QFT of the basis state |x> (the closed form
@@ -228,7 +239,8 @@ int sv_codec_compress_static(const void* values, uint64_t nblocks, int block_log
  * fused pass kernel from then on and zeroes the counters (0 stops recording).
  * sv_get_pass_timing synchronizes and returns the summed kernel time of the recorded
  * passes (ms), their number, and their algorithmic bytes: compressed bytes read plus
- * written, plus 32 bytes of block-table and verbatim-sum traffic per block.
+ * written, plus 64 bytes per block of table traffic (offset and length read and written,
+ * the block summary read and written, the verbatim sum written).
  * ------------------------------------------------------------------------------------- */
 int sv_set_pass_timing(sv_state* s, int on);
 int sv_get_pass_timing(sv_state* s, double* kernel_ms, uint64_t* passes, uint64_t* bytes);

@@ -108,6 +108,7 @@ struct sv_state {
   DevScalars* sc = nullptr;
   unsigned long long* toff[2] = {nullptr, nullptr};
   unsigned int* tlen[2] = {nullptr, nullptr};
+  BlkInfo* binfo[2] = {nullptr, nullptr};
   double* vsum = nullptr;
   double* tree = nullptr;
   double* vroot = nullptr;
@@ -128,6 +129,11 @@ struct sv_state {
   double kernel_ms = 0.0;
   unsigned long long timed_passes = 0;
   unsigned long long io_base = 0;
+  unsigned long long replayed = 0;  // passes re-run after an arena overflow
+  int threads = 0;                  // CTA size of the fused pass (0: default)
+  // passes between status checks: 8 after an overflow, doubling per clean check up to 256
+  // (an overflow poisons every later pass until the check replays them)
+  int sync_every = 16;
 };
 
 namespace {
@@ -195,6 +201,10 @@ void build_args(const sv_state* s, const Logged& lg, PassArgs& a) {
   a.out_id = lg.out_id;
   a.out_off = s->toff[lg.out_id];
   a.out_len = s->tlen[lg.out_id];
+  a.threads = s->threads;
+  a.in_info = s->binfo[lg.in_id];
+  a.out_info = s->binfo[lg.out_id];
+  for (int g = 0; g < 4; ++g) a.pt_src[g] = -1;
   if (lg.basis) {
     a.input_basis = 1;
     a.basis = lg.basis_index;
@@ -248,6 +258,36 @@ void build_args(const sv_state* s, const Logged& lg, PassArgs& a) {
       a.g[e] = lg.G[e];
       a.gf[e] = (float)lg.G[e];
     }
+    // stream pass-through map: slot g keeps the codes of slot src when every row of the
+    // members in g is a unit row (exactly 1) whose column is the same in-block position in
+    // slot src; with in-block controls only src = g (the identity) qualifies
+    a.cmask_high = cm & ~((1ull << s->b) - 1ull);
+    const bool low_ctrl = (cm & ((1ull << s->b) - 1ull)) != 0;
+    int mslot[8], moff[8];
+    for (int m = 0; m < a.K; ++m) {
+      mslot[m] = a.pos_delta[m] / a.nv;
+      moff[m] = a.pos_delta[m] % a.nv;
+    }
+    int src[4] = {-2, -2, -2, -2};
+    for (int jj = 0; jj < a.K; ++jj) {
+      const int g = mslot[jj];
+      int nz = 0, col = -1;
+      a.need[g] |= 1u << g;
+      for (int m = 0; m < a.K; ++m)
+        if (lg.G[2 * (jj * a.K + m)] != 0.0 || lg.G[2 * (jj * a.K + m) + 1] != 0.0) {
+          ++nz;
+          col = m;
+          a.need[g] |= 1u << mslot[m];
+        }
+      int sg = -1;
+      if (nz == 1 && lg.G[2 * (jj * a.K + col)] == 1.0 && lg.G[2 * (jj * a.K + col) + 1] == 0.0 &&
+          moff[col] == moff[jj])
+        sg = mslot[col];
+      if (low_ctrl && sg != g) sg = -1;
+      src[g] = (src[g] == -2 || src[g] == sg) ? sg : -1;
+    }
+    for (int g = 0; g < a.G; ++g) a.pt_src[g] = src[g] < 0 ? -1 : src[g];
+    a.pt_ok = s->dtype == SV_C128 ? 1 : 0;
   }
   a.ngroups = s->nblocks >> a.h;
 }
@@ -287,7 +327,7 @@ int log_step(sv_state* s, Logged&& lg) {
   s->cur ^= 1;
   if (s->sticky_err) return SV_OK;
   s->log.push_back(std::move(lg));
-  if (s->log.size() >= 256) {
+  if (s->log.size() >= (size_t)s->sync_every) {
     const int rc = sv_sync(s);
     if (rc == SV_ERR_CUDA) return rc;
     if (rc) s->sticky_err = rc;
@@ -311,8 +351,20 @@ int read_scalars(sv_state* s, DevScalars* h) {
   return cuda_err(e);
 }
 
+// Give arena `id` (not the live one) at least `want` bytes when the pool has room; keeps
+// the current size otherwise. Its content is not needed: the next pass overwrites it.
+int reserve_arena(sv_state* s, int id, size_t want) {
+  if (s->arena_r[id].bytes >= want) return SV_OK;
+  const size_t old = s->arena_r[id].bytes;
+  region_free(s->pool, &s->arena_r[id]);
+  if (!region_alloc(s->pool, &s->arena_r[id], want) && !region_alloc(s->pool, &s->arena_r[id], old))
+    return SV_ERR_OOM;
+  s->arena[id] = pool_ptr(s->pool, s->arena_r[id].off);
+  return SV_OK;
+}
+
 int grow_arena(sv_state* s, int id, size_t need) {
-  size_t want = std::max(s->arena_r[id].bytes * 2, need + need / 4);
+  size_t want = std::max(s->arena_r[id].bytes + s->arena_r[id].bytes / 2, need + need / 4);
   region_free(s->pool, &s->arena_r[id]);
   if (!region_alloc(s->pool, &s->arena_r[id], want)) {
     if (!region_alloc(s->pool, &s->arena_r[id], need)) return SV_ERR_OOM;
@@ -422,7 +474,7 @@ int sv_create_ex(sv_pool* pool, int n, int sl, int bl, double eb, int dtype, siz
   s->qp.r = 1.0 / s->qp.two;
   s->two2 = s->qp.two * s->qp.two;
   s->nblocks = 1ull << (n - bl);
-  // metadata run: scalars | table 0 | table 1 | vsum | tree scratch | root
+  // metadata run: scalars | tables 0, 1 | block summaries 0, 1 | vsum | tree scratch | root
   const size_t nb = s->nblocks;
   size_t off = 0;
   const size_t o_sc = off;
@@ -435,6 +487,10 @@ int sv_create_ex(sv_pool* pool, int n, int sl, int bl, double eb, int dtype, siz
   off += round_up(nb * 4, 256);
   const size_t o_len1 = off;
   off += round_up(nb * 4, 256);
+  const size_t o_info0 = off;
+  off += round_up(nb * sizeof(BlkInfo), 256);
+  const size_t o_info1 = off;
+  off += round_up(nb * sizeof(BlkInfo), 256);
   const size_t o_vsum = off;
   off += round_up(nb * 8, 256);
   const size_t o_tree = off;
@@ -451,6 +507,8 @@ int sv_create_ex(sv_pool* pool, int n, int sl, int bl, double eb, int dtype, siz
   s->toff[1] = (unsigned long long*)(m + o_off1);
   s->tlen[0] = (unsigned int*)(m + o_len0);
   s->tlen[1] = (unsigned int*)(m + o_len1);
+  s->binfo[0] = (BlkInfo*)(m + o_info0);
+  s->binfo[1] = (BlkInfo*)(m + o_info1);
   s->vsum = (double*)(m + o_vsum);
   s->tree = (double*)(m + o_tree);
   s->vroot = (double*)(m + o_root);
@@ -541,6 +599,11 @@ int sv_sync(sv_state* s) {
     if (rc) return rc;
     if (h.status == 0) {
       s->log.clear();
+      s->sync_every = std::min(256, s->sync_every * 2);
+      // the arena the next pass writes gets room for 1.5x the current state
+      const size_t live = (size_t)h.bump[s->cur];
+      rc = reserve_arena(s, s->cur ^ 1, live + live / 2);
+      if (rc) return rc;
       for (auto& ev : s->ev_pending) {
         float ms = 0.f;
         cudaEventElapsedTime(&ms, ev.first, ev.second);
@@ -555,6 +618,7 @@ int sv_sync(sv_state* s) {
     for (auto& ev : s->ev_pending) s->ev_free.push_back(ev);
     s->ev_pending.clear();
     if (h.status != kStOverflow) return status_to_err(h.status);
+    s->sync_every = 8;
     // find the failed pass in the log
     size_t i = 0;
     while (i < s->log.size() && s->log[i].seq != h.fail_seq) ++i;
@@ -572,6 +636,7 @@ int sv_sync(sv_state* s) {
     for (size_t j = i; j < s->log.size(); ++j) {
       rc = launch_logged(s, s->log[j]);
       if (rc) return rc;
+      s->replayed++;
     }
   }
   return SV_ERR_OOM;
@@ -606,6 +671,12 @@ int sv_norm(sv_state* s, double* out) {
   return SV_OK;
 }
 
+int sv_set_threads(sv_state* s, int threads) {
+  if (!s || s->plain || (threads != 0 && !threads_ok(s->b, threads))) return SV_ERR_ARG;
+  s->threads = threads;
+  return SV_OK;
+}
+
 int sv_stats(sv_state* s, sv_stats_t* out) {
   if (!s || !out) return SV_ERR_ARG;
   int rc = sv_sync(s);
@@ -629,6 +700,8 @@ int sv_stats(sv_state* s, sv_stats_t* out) {
   out->n_escape = h.last.n_escape;
   out->norm = h.norm;
   out->sigma = h.sigma;
+  out->blocks_reused = h.last.reused;
+  out->replayed_passes = s->replayed;
   return SV_OK;
 }
 
@@ -778,7 +851,9 @@ int sv_get_pass_timing(sv_state* s, double* kernel_ms, uint64_t* passes, uint64_
   if (rc) return rc;
   if (kernel_ms) *kernel_ms = s->kernel_ms;
   if (passes) *passes = s->timed_passes;
-  if (bytes) *bytes = (h.io_bytes - s->io_base) + 32ull * s->nblocks * s->timed_passes;
+  // per block: offset + length read (12) and written (12), summary read and written (32),
+  // verbatim sum written (8)
+  if (bytes) *bytes = (h.io_bytes - s->io_base) + 64ull * s->nblocks * s->timed_passes;
   return SV_OK;
 }
 
@@ -937,7 +1012,7 @@ int sv_batch_apply(sv_batch* bt, sv_state* const* states, const sv_gate_t* gates
     cudaError_t r = cudaMemcpyAsync(bt->d_blob, src, bt->blob_bytes, cudaMemcpyHostToDevice, bt->st);
     if (r == cudaSuccess)
       r = launch_pass_batch(d_descs, d_prefix, count, hp[count], s0->b, gmax, kbucket,
-                            s0->dtype == SV_C64 ? 1 : 2, bt->st);
+                            s0->dtype == SV_C64 ? 1 : 2, s0->threads, bt->st);
     if (r == cudaSuccess) r = launch_norm_batch(d_descs, d_trees, d_nb, count, bt->st);
     return r;
   };

@@ -28,9 +28,21 @@ struct Misc {
   uint32_t size;
   unsigned long long out_off;
   int ok;
+  int pt[4];       // pass-through source slot per block of the group (-1: recode)
+  unsigned int dmask;  // blocks of the group to decode
+  int npt;
   int first[34];   // canonical first code per length
   int offs[34];    // first canonical index per length
   int lcount[34];  // codes per length
+};
+
+// Summary of one stored block stream, written with it by every pass and read by the next:
+// enough to re-emit the stream unchanged (with its norm and statistics contributions) when
+// the next pass provably reproduces the block's codes.
+struct BlkInfo {
+  unsigned long long sq_lo;  // exact sum of q^2 over the block (< 2^71), low 64 bits
+  unsigned int sq_hi_nesc;   // bits 0..7: bits 64..71 of the sum; bits 8..31: escapes
+  unsigned int maxq_mode;    // bits 0..28: max |q|; bits 29..30: mode; bit 31: verbatim values
 };
 
 struct __align__(16) PassArgs {
@@ -61,6 +73,16 @@ struct __align__(16) PassArgs {
   DevScalars* sc;
   double* vsum;
   unsigned int seq;
+  // stream pass-through (complex128): block slot g of a group whose high controls are all 1
+  // takes the codes of slot pt_src[g] unchanged (-1: never); need[g] is the mask of the
+  // slots its outputs read
+  int threads;  // CTA size (0: worker_threads(b)); results do not depend on it
+  int pt_ok;
+  int pt_src[4];
+  unsigned int need[4];
+  unsigned long long cmask_high;  // control bits at or above b
+  const BlkInfo* in_info;
+  BlkInfo* out_info;
 };
 
 // Fixed-point form of one gate pass for complex128 (computed once per CTA): output jj, part
@@ -71,6 +93,11 @@ struct FastGate {
   int F;              // fractional bits of W
   int diag;           // the gate matrix is diagonal
   long long margin;   // half-width of the band around a rounding tie sent to the exact path
+  // outputs that are one input times +-1 (identity rows, permutations, phase +-1 / +-i):
+  // source index (member * 2 + component, -1 if not such an output) and sign; their code is
+  // exactly +-q whenever |q| <= qsafe
+  int8_t ssrc[8][2], ssgn[8][2];
+  int qsafe;
   int32_t chi[8][2][8][2], clo[8][2][8][2];
   int32_t idhi, idlo; // the identity scaled by sigma (members whose controls are not all 1)
 };
@@ -147,7 +174,13 @@ __host__ __device__ inline Layout make_layout(int b, int G, int csize) {
   return L;
 }
 
-// One thread per 32-value decode chunk (every thread decodes one chunk), 32 to 256 threads.
+// Default CTA size: one thread per 32-value decode chunk, 32 to 256 threads. Any power of
+// two T with 32 <= T <= 256 and 2 <= 2^(b+1) / T <= 32 works (threads beyond the chunk count
+// idle while decoding); results do not depend on T.
+__host__ __device__ inline bool threads_ok(int b, int t) {
+  const int nv = 2 << b;
+  return t >= 32 && t <= 256 && (t & (t - 1)) == 0 && nv / t >= 2 && nv / t <= 32;
+}
 __host__ __device__ inline int worker_threads(int b) {
   int nv = 2 << b;
   int t = nv / kChunk;
@@ -530,6 +563,46 @@ struct Worker {
   // ------------------------------------------------------------------------------------
   __device__ void encode(int g, unsigned long long blk, const PassArgs& a);
 
+  // Re-emit the input stream of block sb as the output stream of block db: the pass has
+  // been shown to reproduce sb's codes exactly at db's positions, and encoding is a function
+  // of the codes alone, so the recoded stream would be these bytes. The norm partial and
+  // statistics come from sb's summary, as the recode would have added them.
+  __device__ void pass_through(unsigned long long sb, unsigned long long db, const PassArgs& a) {
+    const int tid = threadIdx.x;
+    const uint32_t len = a.in_len[sb];
+    if (tid == 0) {
+      const unsigned long long off = atomicAdd(&a.sc->bump[a.out_id], (unsigned long long)len);
+      m->out_off = off;
+      m->ok = off + len <= a.out_cap;
+      if (!m->ok) {
+        atomicOr(&a.sc->status, kStOverflow);
+        atomicMin(&a.sc->fail_seq, a.seq);
+      }
+      const BlkInfo bi = a.in_info[sb];
+      const unsigned long long lo = bi.sq_lo, hi = bi.sq_hi_nesc & 0xFFu;
+      const unsigned long long old = atomicAdd(&a.sc->acc.sq_lo, lo);
+      const unsigned long long c1 = (old + lo < old) ? 1ull : 0ull;
+      if (hi + c1) atomicAdd(&a.sc->acc.sq_hi, hi + c1);
+      const int mode = (int)((bi.maxq_mode >> 29) & 3u);
+      if (mode != kModeConst) atomicAdd(&a.sc->acc.n_escape, (unsigned long long)(bi.sq_hi_nesc >> 8));
+      atomicAdd(&a.sc->acc.modes[mode], 1ull);
+      atomicAdd(&a.sc->acc.reused, 1ull);
+      a.out_info[db] = bi;
+      if (a.vsum) a.vsum[db] = 0.0;
+    }
+    __syncthreads();
+    if (m->ok) {
+      const uint4* src = (const uint4*)(a.in_arena + a.in_off[sb]);
+      uint4* dst = (uint4*)(a.out_arena + m->out_off);
+      for (uint32_t i = tid; i < len / 16; i += T) dst[i] = src[i];
+      if (tid == 0) {
+        a.out_off[db] = m->out_off;
+        a.out_len[db] = len;
+      }
+    }
+    __syncthreads();
+  }
+
   // complex64: write the verbatim section (u16 positions ascending, raw floats) of block g
   // into its stream at `out`, after the zero fill of the section
   __device__ void write_verbatim_inplace(int g, uint8_t* out, uint32_t body_end, int nverb) {
@@ -707,7 +780,7 @@ __device__ void Worker<Real>::encode(int g, unsigned long long blk, const PassAr
   const int32_t q0 = qb[0], q1 = qb[1];
   int32_t pr = j0 >= 2 ? code(g, j0 - 2) : 0, pi = j0 >= 2 ? code(g, j0 - 1) : 0;
   unsigned long long sqh = 0, sql = 0;
-  uint32_t zmax = 0;
+  uint32_t zmax = 0, amax = 0;
   int nesc = 0;
   bool cst = true;
 #pragma unroll 4
@@ -723,6 +796,8 @@ __device__ void Worker<Real>::encode(int g, unsigned long long blk, const PassAr
     sql += s2 & 0xffffffffull;
     const uint32_t z = zigzag(d);
     zmax = z > zmax ? z : zmax;
+    const uint32_t ac = (uint32_t)(c < 0 ? -c : c);
+    amax = ac > amax ? ac : amax;
     nesc += (d < -kRadius || d > kRadius) ? 1 : 0;
     cst = cst && (c == ((j & 1) ? q1 : q0));
   }
@@ -741,7 +816,8 @@ __device__ void Worker<Real>::encode(int g, unsigned long long blk, const PassAr
   uint32_t* tsk = (uint32_t*)(build + L.sort_off);  // rank-sort scratch
   uint32_t* tsv = tsk + L.sort_n;
   if (!is_const) {
-    width = bit_width(block_reduce_max<uint32_t>(zmax, m->scan));
+    block_reduce_max2_u32(zmax, amax, m->scan);
+    width = bit_width(zmax);
     const uint32_t pack_body = 4u * (((uint32_t)nv * (uint32_t)width + 31u) / 32u);
     // ---- histogram into the hash table (runs of equal symbols merged first) ----
     for (int i = tid; i < L.hs; i += T) {
@@ -1031,6 +1107,17 @@ __device__ void Worker<Real>::encode(int g, unsigned long long blk, const PassAr
     if (nverb) atomicAdd(&a.sc->acc.n_verbatim, (unsigned long long)nverb);
     if (mode != kModeConst) atomicAdd(&a.sc->acc.n_escape, (unsigned long long)m->nesc);
     atomicAdd(&a.sc->acc.modes[mode], 1ull);
+    if (a.out_info) {
+      if (is_const) {
+        const uint32_t a0 = (uint32_t)(q0 < 0 ? -q0 : q0), a1 = (uint32_t)(q1 < 0 ? -q1 : q1);
+        amax = a0 > a1 ? a0 : a1;
+      }
+      BlkInfo bi;
+      bi.sq_lo = lo;
+      bi.sq_hi_nesc = (unsigned int)(hi & 0xFFull) | ((unsigned int)(mode != kModeConst ? m->nesc : 0) << 8);
+      bi.maxq_mode = (amax & 0x1FFFFFFFu) | ((unsigned int)mode << 29) | (nverb_raw ? 0x80000000u : 0u);
+      a.out_info[blk] = bi;
+    }
   }
   const double vs = nverb > 0 ? verbatim_square_tree(g) : 0.0;
   if (tid == 0 && a.vsum) a.vsum[blk] = vs;

@@ -40,6 +40,7 @@ struct PassAcc {
   unsigned long long sq_lo, sq_hi;  // exact sum of q^2 (128-bit)
   unsigned long long n_verbatim, n_escape;
   unsigned long long modes[3];
+  unsigned long long reused;  // blocks whose stream was re-emitted unchanged (pass-through)
 };
 
 struct DevScalars {
@@ -193,6 +194,29 @@ __device__ __forceinline__ T block_reduce_max(T v, T* ws) {
   T r = ws[0];
   __syncthreads();
   return r;
+}
+
+// Two block-wide maxima with one pair of barriers (ws: 2 words per warp).
+__device__ __forceinline__ void block_reduce_max2_u32(uint32_t& a, uint32_t& b, uint32_t* ws) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const uint32_t ya = __shfl_xor_sync(0xffffffffu, a, o), yb = __shfl_xor_sync(0xffffffffu, b, o);
+    a = a > ya ? a : ya;
+    b = b > yb ? b : yb;
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  if (lane == 0) {
+    ws[2 * wid] = a;
+    ws[2 * wid + 1] = b;
+  }
+  __syncthreads();
+  uint32_t ra = 0, rb = 0;
+  for (int w = 0; w < nw; ++w) {
+    ra = ws[2 * w] > ra ? ws[2 * w] : ra;
+    rb = ws[2 * w + 1] > rb ? ws[2 * w + 1] : rb;
+  }
+  __syncthreads();
+  a = ra;
+  b = rb;
 }
 
 __device__ __forceinline__ unsigned long long block_reduce_sum_u64(unsigned long long v,

@@ -13,7 +13,7 @@ cudaError_t launch_pass(const PassArgs& a, int dtype, cudaStream_t st);
 // batched norm finalization (verbatim-sum tree per state in one CTA, then N and sigma).
 cudaError_t launch_pass_batch(const PassArgs* descs, const unsigned long long* gprefix, int nstates,
                               unsigned long long total_groups, int b, int Gmax, int Kmax, int dtype,
-                              cudaStream_t st);
+                              int threads, cudaStream_t st);
 cudaError_t launch_norm_batch(const PassArgs* descs, const double* const* trees, const unsigned long long* nblocks,
                               int nstates, cudaStream_t st);
 // Pairwise (level by level) sum of n = 2^k per-block verbatim sums into root[0].

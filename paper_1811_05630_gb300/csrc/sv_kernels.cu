@@ -75,7 +75,43 @@ __device__ void fast_prepare(FastGate* fg, const PassArgs& a, double sigma) {
     *lo = (int32_t)(v & 0x7fffffffll);
   };
   fix(s1, &fg->idhi, &fg->idlo);
+  // |q| <= qsafe gives rint of the exact chain for q * s1 equal to q: |q| |s1' - 1| plus the
+  // chain's error (<= 2^-19 R here) stays below 1/2 - 2^-18 (s1' the exact scale, within
+  // 2^-51 of s1)
+  {
+    const double dev = fabs(s1 - 1.0) + scalbn(1.0, -50);
+    const double lim = (0.5 - scalbn(1.0, -18) - R * scalbn(1.0, -19)) / dev;
+    fg->qsafe = lim >= 536870000.0 ? 536870000 : (lim > 0.0 ? (int)lim : -1);
+  }
+  for (int jj = 0; jj < 8; ++jj)
+    for (int p = 0; p < 2; ++p) {
+      fg->ssrc[jj][p] = -1;
+      fg->ssgn[jj][p] = 1;
+    }
   if (!a.apply_gate) return;
+  for (int jj = 0; jj < K; ++jj) {
+    int nz = 0, mz = -1;
+    for (int m = 0; m < K; ++m)
+      if (a.g[2 * (jj * K + m)] != 0.0 || a.g[2 * (jj * K + m) + 1] != 0.0) {
+        ++nz;
+        mz = m;
+      }
+    if (nz != 1) continue;
+    const double gr = a.g[2 * (jj * K + mz)], gi = a.g[2 * (jj * K + mz) + 1];
+    if (gi == 0.0 && (gr == 1.0 || gr == -1.0)) {  // (+-1) (x + iy)
+      const int sg = gr > 0 ? 1 : -1;
+      fg->ssrc[jj][0] = (int8_t)(2 * mz);
+      fg->ssgn[jj][0] = (int8_t)sg;
+      fg->ssrc[jj][1] = (int8_t)(2 * mz + 1);
+      fg->ssgn[jj][1] = (int8_t)sg;
+    } else if (gr == 0.0 && (gi == 1.0 || gi == -1.0)) {  // (+-i) (x + iy) = -+y +- ix
+      const int sg = gi > 0 ? 1 : -1;
+      fg->ssrc[jj][0] = (int8_t)(2 * mz + 1);
+      fg->ssgn[jj][0] = (int8_t)-sg;
+      fg->ssrc[jj][1] = (int8_t)(2 * mz);
+      fg->ssgn[jj][1] = (int8_t)sg;
+    }
+  }
   int diag = 1;
   for (int jj = 0; jj < K; ++jj)
     for (int m = 0; m < K; ++m) {
@@ -216,11 +252,45 @@ __device__ __forceinline__ void pass_group(Worker<Real>& w, const PassArgs& a, c
   }
   __syncthreads();
   if (threadIdx.x < 4) w.vout_cnt[threadIdx.x] = 0;
+  // ---- stream pass-through (complex128) ----
+  // Block slot g keeps the codes of slot src (src = g where the gate acts as the identity on
+  // it: the group's high controls are not all 1, or its rows are unit rows; another slot for
+  // a +1 permutation across blocks) when that slot holds no verbatim value and every |q| is
+  // within qsafe: then each output code equals its input code exactly (the same argument as
+  // the single-term shortcut below), and the block's stream is the source stream.
+  bool any_pt = false;
+  if (kFast && a.pt_ok && fg->F >= 0) {
+    if (threadIdx.x == 0) {
+      const bool hc = ((blks[0] << a.b) & a.cmask_high) == a.cmask_high;
+      unsigned int dmask = 0;
+      int npt = 0;
+      for (int g = 0; g < a.G; ++g) {
+        int src = hc ? a.pt_src[g] : g;
+        if (src >= 0) {
+          const unsigned int mm = a.in_info[blks[src]].maxq_mode;
+          if ((mm & 0x80000000u) || (long long)(mm & 0x1FFFFFFFu) > (long long)fg->qsafe) src = -1;
+        }
+        w.m->pt[g] = src;
+        if (src >= 0) ++npt;
+        else dmask |= hc ? a.need[g] : (1u << g);
+      }
+      w.m->dmask = dmask;
+      w.m->npt = npt;
+    }
+    __syncthreads();
+    any_pt = w.m->npt > 0;
+    if (w.m->npt == a.G) {
+      for (int g = 0; g < a.G; ++g) w.pass_through(blks[w.m->pt[g]], blks[g], a);
+      return;
+    }
+  }
   // ---- Decompress(S) ----
   for (int g = 0; g < a.G; ++g) {
     if (a.input_basis) {
       const int pos = ((a.basis >> a.b) == blks[g]) ? 2 * (int)(a.basis & (unsigned long long)(B - 1)) : -1;
       w.load_basis(g, pos);
+    } else if (any_pt && !((w.m->dmask >> g) & 1u)) {
+      w.load_basis(g, -1);  // read by no recoded block: zeros
     } else {
       w.decode(g, a.in_arena + a.in_off[blks[g]], a.in_len[blks[g]]);
     }
@@ -257,31 +327,46 @@ __device__ __forceinline__ void pass_group(Worker<Real>& w, const PassArgs& a, c
           if (jj < a.K) {
 #pragma unroll
             for (int p = 0; p < 2; ++p) {
-              long long sh = 0, sl = 0;
-              if (ctrl && fg->diag) {
+              // outputs that are +-1 times one input: exact without arithmetic when small
+              const int ssrc = ctrl ? fg->ssrc[jj][p] : 2 * jj + p;
+              bool done = false;
+              if (ssrc >= 0) {
+                int32_t qq = 0;
 #pragma unroll
-                for (int c = 0; c < 2; ++c) {
-                  const long long qq = qv[2 * jj + c];
-                  sh += qq * fg->chi[jj][p][jj][c];
-                  sl += (qq * fg->clo[jj][p][jj][c]) >> 4;
+                for (int e = 0; e < 2 * KM; ++e)
+                  if (e == ssrc) qq = qv[e];
+                if ((qq < 0 ? -qq : qq) <= fg->qsafe) {
+                  out[2 * jj + p] = (ctrl && fg->ssgn[jj][p] < 0) ? -qq : qq;
+                  done = true;
                 }
-              } else if (ctrl) {
-#pragma unroll
-                for (int m = 0; m < KM; ++m)
-                  if (m < a.K) {
-#pragma unroll
-                    for (int c = 0; c < 2; ++c) {
-                      const long long qq = qv[2 * m + c];
-                      sh += qq * fg->chi[jj][p][m][c];
-                      sl += (qq * fg->clo[jj][p][m][c]) >> 4;
-                    }
-                  }
-              } else {
-                const long long qq = qv[2 * jj + p];
-                sh = qq * fg->idhi;
-                sl = (qq * fg->idlo) >> 4;
               }
-              if (!fast_round(sh + (sl >> 27), F, margin, &out[2 * jj + p])) exact_mask |= 1u << (2 * jj + p);
+              if (!done) {
+                long long sh = 0, sl = 0;
+                if (ctrl && fg->diag) {
+  #pragma unroll
+                  for (int c = 0; c < 2; ++c) {
+                    const long long qq = qv[2 * jj + c];
+                    sh += qq * fg->chi[jj][p][jj][c];
+                    sl += (qq * fg->clo[jj][p][jj][c]) >> 4;
+                  }
+                } else if (ctrl) {
+  #pragma unroll
+                  for (int m = 0; m < KM; ++m)
+                    if (m < a.K) {
+  #pragma unroll
+                      for (int c = 0; c < 2; ++c) {
+                        const long long qq = qv[2 * m + c];
+                        sh += qq * fg->chi[jj][p][m][c];
+                        sl += (qq * fg->clo[jj][p][m][c]) >> 4;
+                      }
+                    }
+                } else {
+                  const long long qq = qv[2 * jj + p];
+                  sh = qq * fg->idhi;
+                  sl = (qq * fg->idlo) >> 4;
+                }
+                if (!fast_round(sh + (sl >> 27), F, margin, &out[2 * jj + p])) exact_mask |= 1u << (2 * jj + p);
+              }
             }
           }
         double zx[2 * KM];
@@ -307,7 +392,10 @@ __device__ __forceinline__ void pass_group(Worker<Real>& w, const PassArgs& a, c
   }
   __syncthreads();
   // ---- Compress(S) ----
-  for (int g = 0; g < a.G; ++g) w.encode(g, blks[g], a);
+  for (int g = 0; g < a.G; ++g) {
+    if (any_pt && w.m->pt[g] >= 0) w.pass_through(blks[w.m->pt[g]], blks[g], a);
+    else w.encode(g, blks[g], a);
+  }
 }
 
 template <typename Real, int KM>
@@ -393,7 +481,8 @@ __global__ void __launch_bounds__(256) k_pass_batch(const PassArgs* __restrict__
 
 template <typename Real, int KM>
 static cudaError_t launch_pass_batch_k(const PassArgs* descs, const unsigned long long* gprefix, int nstates,
-                                       unsigned long long total_groups, int b, int Gmax, cudaStream_t st) {
+                                       unsigned long long total_groups, int b, int Gmax, int threads,
+                                       cudaStream_t st) {
   const Layout L = make_layout(b, Gmax, (int)sizeof(Real));
   static bool configured = false;
   if (!configured) {
@@ -402,7 +491,7 @@ static cudaError_t launch_pass_batch_k(const PassArgs* descs, const unsigned lon
     configured = true;
   }
   if (L.total > 227 * 1024) return cudaErrorInvalidValue;
-  const int T = worker_threads(b);
+  const int T = threads_ok(b, threads) ? threads : worker_threads(b);
   unsigned long long grid = total_groups;
   if (grid > 0x7fffffffull) grid = 0x7fffffffull;
   if (grid == 0) return cudaSuccess;
@@ -412,15 +501,16 @@ static cudaError_t launch_pass_batch_k(const PassArgs* descs, const unsigned lon
 
 cudaError_t launch_pass_batch(const PassArgs* descs, const unsigned long long* gprefix, int nstates,
                               unsigned long long total_groups, int b, int Gmax, int Kmax, int dtype,
-                              cudaStream_t st) {
+                              int threads, cudaStream_t st) {
+  const unsigned long long tg = total_groups;
   if (dtype == 1) {
-    if (Kmax <= 2) return launch_pass_batch_k<float, 2>(descs, gprefix, nstates, total_groups, b, Gmax, st);
-    if (Kmax <= 4) return launch_pass_batch_k<float, 4>(descs, gprefix, nstates, total_groups, b, Gmax, st);
-    return launch_pass_batch_k<float, 8>(descs, gprefix, nstates, total_groups, b, Gmax, st);
+    if (Kmax <= 2) return launch_pass_batch_k<float, 2>(descs, gprefix, nstates, tg, b, Gmax, threads, st);
+    if (Kmax <= 4) return launch_pass_batch_k<float, 4>(descs, gprefix, nstates, tg, b, Gmax, threads, st);
+    return launch_pass_batch_k<float, 8>(descs, gprefix, nstates, tg, b, Gmax, threads, st);
   }
-  if (Kmax <= 2) return launch_pass_batch_k<double, 2>(descs, gprefix, nstates, total_groups, b, Gmax, st);
-  if (Kmax <= 4) return launch_pass_batch_k<double, 4>(descs, gprefix, nstates, total_groups, b, Gmax, st);
-  return launch_pass_batch_k<double, 8>(descs, gprefix, nstates, total_groups, b, Gmax, st);
+  if (Kmax <= 2) return launch_pass_batch_k<double, 2>(descs, gprefix, nstates, tg, b, Gmax, threads, st);
+  if (Kmax <= 4) return launch_pass_batch_k<double, 4>(descs, gprefix, nstates, tg, b, Gmax, threads, st);
+  return launch_pass_batch_k<double, 8>(descs, gprefix, nstates, tg, b, Gmax, threads, st);
 }
 
 template <typename Real, int KM>
@@ -433,7 +523,7 @@ static cudaError_t launch_pass_k(const PassArgs& a, cudaStream_t st) {
     configured = true;
   }
   if (L.total > 227 * 1024) return cudaErrorInvalidValue;
-  const int T = worker_threads(a.b);
+  const int T = threads_ok(a.b, a.threads) ? a.threads : worker_threads(a.b);
   unsigned long long grid = a.ngroups;
   if (grid > 0x7fffffffull) grid = 0x7fffffffull;
   k_pass<Real, KM><<<(unsigned int)grid, T, L.total, st>>>(a);
@@ -518,6 +608,7 @@ __global__ void k_finalize(DevScalars* sc, const double* root, double two2, int 
   sc->acc.sq_lo = sc->acc.sq_hi = 0;
   sc->acc.n_verbatim = sc->acc.n_escape = 0;
   sc->acc.modes[0] = sc->acc.modes[1] = sc->acc.modes[2] = 0;
+  sc->acc.reused = 0;
   sc->bump[reset_id] = 0;
   sc->pass_index++;
 }
@@ -594,6 +685,7 @@ __global__ void k_finalize_batch(const PassArgs* __restrict__ descs, const doubl
   sc->acc.sq_lo = sc->acc.sq_hi = 0;
   sc->acc.n_verbatim = sc->acc.n_escape = 0;
   sc->acc.modes[0] = sc->acc.modes[1] = sc->acc.modes[2] = 0;
+  sc->acc.reused = 0;
   sc->bump[reset_id] = 0;
   sc->pass_index++;
 }

@@ -45,6 +45,7 @@ class Stats(ctypes.Structure):
         ("blocks_const", ctypes.c_uint64), ("blocks_huff", ctypes.c_uint64),
         ("blocks_pack", ctypes.c_uint64), ("n_verbatim", ctypes.c_uint64),
         ("n_escape", ctypes.c_uint64), ("norm", ctypes.c_double), ("sigma", ctypes.c_double),
+        ("blocks_reused", ctypes.c_uint64), ("replayed_passes", ctypes.c_uint64),
     ]
 
     def as_dict(self):
@@ -68,6 +69,7 @@ _SIGS = {
     "sv_reset_basis": ([_vp, _u64], _i),
     "sv_apply_gate": ([_vp, _vp, _vp, _i, _vp, _i], _i),
     "sv_sync": ([_vp], _i),
+    "sv_set_threads": ([_vp, _i], _i),
     "sv_measure_probs": ([_vp, _vp, _i, _vp], _i),
     "sv_amplitudes": ([_vp, _vp, _sz, _vp], _i),
     "sv_read_amplitudes": ([_vp, _u64, _u64, _vp], _i),
@@ -169,6 +171,10 @@ class State:
         v = ctypes.c_double()
         _check(_L.sv_norm(self._h, ctypes.byref(v)), "sv_norm")
         return v.value
+
+    def set_threads(self, threads: int) -> None:
+        """CTA size of the fused pass (0: default); results do not depend on it."""
+        _check(_L.sv_set_threads(self._h, int(threads)), "sv_set_threads")
 
     def stats(self) -> dict:
         st = Stats()

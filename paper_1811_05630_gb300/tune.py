@@ -1,0 +1,101 @@
+"""Autotuner for the block size (block_log2) and the CTA size of the fused pass.
+
+The block size sets the codec's parallel unit: small blocks give more CTAs per pass and
+more CTAs per SM (less shared memory each), large blocks amortize the per-block codebook
+and headers. The CTA size (threads per block-group) trades per-block latency against CTAs
+resident per SM (registers). The best pair depends on the state size, dtype, error bound and
+circuit, so the tuner times a few gate passes of a representative circuit for each candidate
+on the GPU (fused-kernel CUDA events) and keeps the fastest. Neither knob changes results.
+Results are cached in a JSON file keyed by (GPU name, dtype, qubits, error bound, circuit
+kind).
+"""
+from __future__ import annotations
+
+import json
+import os
+from typing import Dict, Iterable, List, Optional, Sequence
+
+import torch
+
+from . import sv
+from .circuits import Gate
+
+CACHE = os.environ.get("SV_TUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "sv_tune.json"))
+
+
+def _key(n: int, dtype: int, eb: float, kind: str) -> str:
+    return "%s|%d|%d|%.3g|%s" % (torch.cuda.get_device_name(), dtype, n, eb, kind)
+
+
+def _load() -> Dict[str, dict]:
+    try:
+        with open(CACHE) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _store(d: Dict[str, dict]) -> None:
+    try:
+        os.makedirs(os.path.dirname(CACHE), exist_ok=True)
+        with open(CACHE + ".tmp", "w") as f:
+            json.dump(d, f, indent=1)
+        os.replace(CACHE + ".tmp", CACHE)
+    except OSError:
+        pass
+
+
+def thread_candidates(b: int) -> List[int]:
+    """CTA sizes the fused pass accepts for block size b (powers of two, 32..256, 2 to 32
+    values per thread)."""
+    nv = 2 << b
+    return [t for t in (32, 64, 128, 256) if 2 <= nv // t <= 32]
+
+
+def probe(pool: sv.Pool, n: int, dtype: int, eb: float, b: int, prefix: Sequence[Gate], timed: Sequence[Gate],
+          basis: int = 0, threads: int = 0) -> float:
+    """Fused-kernel milliseconds per pass for `timed` after `prefix`, at block size b and CTA
+    size `threads` (0: the default)."""
+    st = sv.State(pool, n, n, eb, dtype, block_log2=b)
+    try:
+        st.set_threads(threads)
+        st.reset_basis(basis)
+        st.run(prefix)
+        st.sync()
+        st.set_pass_timing(True)
+        st.run(timed)
+        ms, npass, _ = st.pass_timing()
+        return ms / max(npass, 1)
+    finally:
+        st.close()
+
+
+def best_config(n: int, dtype: int, eb: float, kind: str, prefix: Sequence[Gate], timed: Sequence[Gate],
+                basis: int = 0, candidates: Iterable[int] = (8, 9, 10, 11, 12), pool: Optional[sv.Pool] = None,
+                use_cache: bool = True) -> dict:
+    """Tune (block_log2, threads) for a workload; returns {"block_log2": b, "threads": T,
+    "ms_per_pass": {"b/T": ms}}."""
+    key = _key(n, dtype, eb, kind)
+    cache = _load() if use_cache else {}
+    if key in cache and "threads" in cache[key]:
+        return cache[key]
+    own = pool is None
+    if own:
+        pool = sv.Pool(max(1 << 30, (24 if dtype == 2 else 12) << n))
+    times: Dict[tuple, float] = {}
+    try:
+        for b in candidates:
+            if b > n:
+                continue
+            for t in thread_candidates(b):
+                times[(b, t)] = probe(pool, n, dtype, eb, b, prefix, timed, basis, threads=t)
+    finally:
+        if own:
+            pool.close()
+    best = min(times, key=times.get)
+    res = {"block_log2": best[0], "threads": best[1],
+           "ms_per_pass": {"%d/%d" % k: v for k, v in sorted(times.items())}}
+    if use_cache:
+        cache[key] = res
+        _store(cache)
+    return res

@@ -149,6 +149,83 @@ def test_multi_target_controlled_gates_bit_exact(sv, pool, dtype):
     run_compare(sv, pool, n, 8, b, dtype, 1e-5, C.seeded_index(9, n), gates, every=4)
 
 
+def _gate(m, targets, controls=(), name=""):
+    return C.Gate(np.asarray(m, dtype=np.complex128), tuple(targets), tuple(controls), name)
+
+
+def run_compare_reuse(sv, pool, n, b, dtype, eb, x, gates, threads=0):
+    """run_compare, gate by gate, summing the blocks each pass re-emitted unchanged."""
+    st = sv.State(pool, n, n, eb, dtype, block_log2=b)
+    reused = 0
+    try:
+        if threads:
+            st.set_threads(threads)
+        st.reset_basis(x)
+        cs = oracle.CompressedSim(n, n, b, dtype, eb, x)
+        for i, g in enumerate(gates):
+            st.apply(g.matrix, g.targets, g.controls)
+            cs.apply(g.matrix, g.targets, g.controls)
+            reused += st.stats()["blocks_reused"]
+            assert_same_state(st, cs, "gate %d %s" % (i, g.name))
+        return reused
+    finally:
+        st.close()
+
+
+def test_stream_pass_through_bit_exact(sv, pool):
+    # complex128 blocks whose codes a pass provably reproduces (controls above the block not
+    # all 1, unit rows, +1 permutations across blocks) re-emit their stream; every pass
+    # must still equal the oracle's full recode byte for byte
+    n, b = 11, 5
+    X = [[0, 1], [1, 0]]
+    CNOT_like = [[1, 0, 0, 0], [0, 0, 0, 1], [0, 0, 1, 0], [0, 1, 0, 0]]  # X on t1 when t0 = 1
+    gates = C.qft(n)[:40] + [
+        _gate(X, (9,), (), "X_high"),
+        _gate(X, (7,), (8, 10), "CCX_high"),
+        _gate(X, (8,), (2,), "CX_lowctrl"),
+        _gate(C.SWAP, (6, 10), (), "SWAP_hh"),
+        _gate(C.SWAP, (1, 9), (), "SWAP_lh"),
+        _gate(CNOT_like, (7, 9), (), "CX_hh"),
+        _gate(CNOT_like, (3, 8), (), "CX_lh"),
+        _gate(np.diag([1, 1j]), (10,), (), "S_high"),
+        _gate(np.diag([-1, 1]), (6,), (), "Zneg_high"),
+        _gate(C.H, (9,), (), "H_high"),
+    ] + C.qft(n)[40:80]
+    reused = run_compare_reuse(sv, pool, n, b, oracle.C128, 1e-6, C.seeded_index(3, n), gates)
+    assert reused > 0
+
+
+def test_pass_through_rejects_verbatim_and_rescaled_blocks(sv, pool):
+    # Grover at eb 4e-10 stores the large marked amplitude verbatim (|x| > 2^29 * 2eb), and
+    # a non-unitary gate moves sigma far from 1: blocks with a verbatim value or a code
+    # beyond the safe range must be recoded, and the result still equals the oracle's
+    n, b = 10, 5
+    marked = C.seeded_index(12, n)
+    gates = C.grover(n, marked, 8)  # marked amplitude sin(17 asin(2^-5)) = 0.51 > 0.43
+    gates += [_gate(np.diag([1.0, 0.8]), (9,), (), "shrink"), _gate(np.diag([1, -1]), (2,), (8,), "CZ_hc"),
+              _gate([[0, 1], [1, 0]], (7,), (), "X_high")]
+    reused = run_compare_reuse(sv, pool, n, b, oracle.C128, 4e-10, 0, gates)
+    assert reused > 0
+
+
+@pytest.mark.parametrize("threads", [64, 128, 256])
+def test_cta_size_does_not_change_results(sv, pool, threads):
+    n, b = 12, 10  # default CTA size 64; 128 and 256 idle part of the CTA while decoding
+    gates = C.qft(n)[:20] + C.random_brickwork(n, 1, seed=8)
+    run_compare_reuse(sv, pool, n, b, oracle.C128, 1e-7, C.seeded_index(6, n), gates, threads=threads)
+
+
+def test_cta_size_checked(sv, pool):
+    st = sv.State(pool, 12, 12, 1e-6, oracle.C128, block_log2=10)
+    try:
+        for bad in (16, 32, 48, 512, 1024):
+            with pytest.raises(sv.SvError):
+                st.set_threads(bad)
+        st.set_threads(0)
+    finally:
+        st.close()
+
+
 def test_arena_overflow_is_replayed(sv, pool):
     # 20 qubits starting from 2 MiB arenas: the random circuit's streams (about 3.5 MB)
     # outgrow them; sv_sync grows the arena to what the pass asked for and replays, and the
@@ -158,6 +235,7 @@ def test_arena_overflow_is_replayed(sv, pool):
     stats, _ = run_compare(sv, pool, n, 14, b, oracle.C128, 1e-7, 0, gates, every=len(gates),
                            arena_bytes=2 << 20)
     assert stats["compressed_bytes"] > 2 << 20
+    assert stats["replayed_passes"] > 0
 
 
 @pytest.mark.parametrize("dtype,tol", [(oracle.C128, 1e-12), (oracle.C64, 1e-5)])
