@@ -111,6 +111,37 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def source_digest() -> str:
+    """Digest of the kernel sources, to tie an ncu traffic figure to the code it measured."""
+    import hashlib
+
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1811_05630_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(f.encode())
+            with open(os.path.join(d, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload: str, block_log2: int, threads: int, compact: bool):
+    """DRAM bytes per fused-pass launch from the committed ncu summary, when it was taken on
+    these exact kernel sources and launch configuration; None otherwise."""
+    path = os.path.join(ROOT, "profiles", "k_pass_%s.md" % workload)
+    try:
+        with open(path) as f:
+            for line in f:
+                if line.startswith("TRAFFIC "):
+                    kv = dict(x.split("=", 1) for x in line.split()[1:])
+                    if (kv.get("digest") == source_digest() and int(kv.get("b", -1)) == block_log2
+                            and int(kv.get("threads", -1)) == threads and int(kv.get("compact", -1)) == int(compact)):
+                        return float(kv["bytes_per_launch"])
+    except (OSError, ValueError, KeyError):
+        pass
+    return None
+
+
 def peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -206,11 +237,14 @@ def run_ours(args, rank, world, dist):
                                  basis=wl["basis"], use_cache=False)
         wl["block_log2"] = tuned["block_log2"]
         wl["threads"] = tuned["threads"]
+        wl["compact"] = tuned["compact"]
     i0 = start_of_dense_stage(wl)
     need = args.warmup + args.steps
     assert i0 + need <= len(gates), "not enough gates for the requested steps"
     if args.threads:
         wl["threads"] = args.threads
+    if args.compact:
+        wl["compact"] = True
     pool_bytes = int(args.pool_gb * (1 << 30))
     pool = sv.Pool(pool_bytes)
     arena = args.arena_mb << 20
@@ -225,6 +259,7 @@ def run_ours(args, rank, world, dist):
                   arena_bytes=arena)
     if wl.get("threads"):
         st.set_threads(wl["threads"])
+    st.set_compact(bool(wl.get("compact")))
     st.reset_basis(wl["basis"])
     st.run(gates[:i0])
     for g in gates[i0:i0 + args.warmup]:
@@ -290,8 +325,11 @@ def run_ours(args, rank, world, dist):
         pk = peaks()
         kern_s = kern_ms * 1e-3
         achieved = alg_bytes / kern_s / 1e9 if kern_s > 0 else 0.0
+        T = wl.get("threads") or min(256, max(32, (2 << wl["block_log2"]) // 32))
         roof = {"bound": "hbm", "achieved": achieved, "peak": pk.get("hbm_gbs"), "unit": "GB/s",
-                "frac": achieved / pk.get("hbm_gbs", 1.0), "traffic": None,
+                "frac": achieved / pk.get("hbm_gbs", 1.0),
+                "traffic": recorded_traffic(wl["name"], wl["block_log2"], T, bool(wl.get("compact"))),
+                "source_digest": source_digest(),
                 "kernel": "k_pass<double>", "kernel_ms_per_launch": kern_ms / max(npass, 1),
                 "alg_bytes_per_launch": alg_bytes / max(npass, 1),
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "fallback" not in pk else "fallback"}
@@ -327,14 +365,15 @@ def run_ours(args, rank, world, dist):
         fid = None
         if args.fidelity and wl["name"] == "grover20":
             fid = full_grover_fidelity(sv, wl)
-        launches_per_pass = 2 + max(1, math.ceil(math.log(max(2, 1 << (n - wl["block_log2"])), 2048)))
+        launches_per_pass = 2  # the fused pass and the one-CTA norm kernel
         result = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": len(timed),
             "warmup": args.warmup, "ms_per_step": ms / len(timed), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if wl["dtype"] == 2 else "f32",
             "data": "synthetic",
             "config": {"workload": wl["desc"], "block_log2": wl["block_log2"],
-                       "threads_per_cta": wl.get("threads") or "default", "autotune": tuned,
+                       "threads_per_cta": wl.get("threads") or "default",
+                       "register_capped_build": bool(wl.get("compact")), "autotune": tuned,
                        "arena_bytes": arena, "replayed_passes_in_timed_region": replays,
                        "parallelism": "replicas",
                        "l2": "flushed between timed steps (512 MiB write, untimed); compressed state %d B"
@@ -382,10 +421,14 @@ def run_full_circuit(args):
     pool = sv.Pool(int(args.pool_gb * (1 << 30)))
     st = sv.State(pool, n, wl["slice_log2"], wl["eb"], wl["dtype"], block_log2=wl["block_log2"],
                   arena_bytes=args.arena_mb << 20)
+    if args.threads:
+        st.set_threads(args.threads)
+    st.set_compact(args.compact)
     st.reset_basis(wl["basis"])
     st.sync()
     raw = (16 if wl["dtype"] == 2 else 8) << n
     per_gate = []
+    reused = 0
     stream = torch.cuda.current_stream()
     t_all = time.time()
     kern_total = 0.0
@@ -395,6 +438,7 @@ def run_full_circuit(args):
             st.apply(g.matrix, g.targets, g.controls)
             stt = st.stats()  # synchronizes: per-gate compressed size
             per_gate.append(stt["compressed_bytes"])
+            reused += stt["blocks_reused"]
     wall = time.time() - t_all
     kern_ms, npass, alg_bytes = st.pass_timing()
     x = wl["basis"]
@@ -408,7 +452,10 @@ def run_full_circuit(args):
     norm = st.norm()
     samp = np.abs(amps) ** 2 / norm * (1 << n)
     res = {
-        "workload": wl["desc"], "block_log2": wl["block_log2"], "gates": len(gates),
+        "workload": wl["desc"], "block_log2": wl["block_log2"], "threads_per_cta": args.threads or "default",
+        "register_capped_build": args.compact,
+        "gates": len(gates), "blocks_reused_fraction": reused / (len(gates) * stt["n_blocks"]),
+        "replayed_passes": stt["replayed_passes"],
         "amp_updates_per_s_wall": (1 << n) * len(gates) / wall,
         "amp_updates_per_s_kernel": (1 << n) * npass / (kern_ms * 1e-3) if kern_ms else None,
         "kernel_ms_total": kern_ms, "wall_s": wall, "fused_kernel_gbs": alg_bytes / (kern_ms * 1e-3) / 1e9,
@@ -475,7 +522,8 @@ def run_serving(args):
     out["arrived_within_limit"] = arrived
     out["offered_within_limit_amp_updates_per_s"] = sum(r.amp_updates for r in reqs if r.arrival <= out["wall_s"]) / out["wall_s"]
     out["config"] = {"requests": args.serve_count, "rate_per_s": args.serve_rate, "budget_gb": args.serve_budget_gb,
-                     "time_limit_s": args.serve_seconds, "block_log2": 10, "max_batch": 64, "graphs": True}
+                     "time_limit_s": args.serve_seconds, "block_log2": 10, "threads_per_cta": 128, "max_batch": 64,
+                     "graphs": True}
     out["clocks"] = clk.summary()
     srv.close()
     return out
@@ -490,6 +538,7 @@ def main():
     ap.add_argument("--workload", default="grover20", choices=["grover20", "qft34", "qft12", "random30"])
     ap.add_argument("--block-log2", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0, help="CTA size of the fused pass (0: tuned/default)")
+    ap.add_argument("--compact", action="store_true", help="register-capped build of the fused pass")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="use the workload's fixed block size instead of tuning it")
     ap.add_argument("--pool-gb", type=float, default=8.0)

@@ -176,6 +176,12 @@ int sv_stats(sv_state* s, sv_stats_t* out);
  * Results (streams, norms) do not depend on it. SV_ERR_ARG for other values or a plain
  * state. A batch runs with the setting of its first state. */
 int sv_set_threads(sv_state* s, int threads);
+
+/* Select (on != 0) the register-capped build of the fused pass for 1- and 2-qubit gates
+ * (64 registers per thread, so that four 256-thread CTAs fit on an SM; larger gates keep the
+ * default build). An autotuning knob with no counterpart in the paper; results do not
+ * depend on it. SV_ERR_ARG for a plain state. Batches ignore it. */
+int sv_set_compact(sv_state* s, int on);
 int sv_norm(sv_state* s, double* out);
 
 /* Overlap with the exact QFT of the basis state |x> (the closed form

@@ -111,7 +111,6 @@ struct sv_state {
   BlkInfo* binfo[2] = {nullptr, nullptr};
   double* vsum = nullptr;
   double* tree = nullptr;
-  double* vroot = nullptr;
   uint8_t* arena[2] = {nullptr, nullptr};
   int cur = 0;
   unsigned int seq = 0;
@@ -131,9 +130,12 @@ struct sv_state {
   unsigned long long io_base = 0;
   unsigned long long replayed = 0;  // passes re-run after an arena overflow
   int threads = 0;                  // CTA size of the fused pass (0: default)
-  // passes between status checks: 8 after an overflow, doubling per clean check up to 256
-  // (an overflow poisons every later pass until the check replays them)
+  bool compact = false;             // register-capped build of the pass (1- and 2-qubit gates)
+  // passes between status checks: every pass while the state grows, 8 after an overflow,
+  // doubling per clean check up to 256 (an overflow poisons every later pass until the
+  // check replays them)
   int sync_every = 16;
+  size_t last_live = 0;  // stream bytes of the state at the last clean check
 };
 
 namespace {
@@ -192,6 +194,7 @@ void build_args(const sv_state* s, const Logged& lg, PassArgs& a) {
   a.two_r = s->qp.two * s->qp.r;
   a.sc = s->sc;
   a.vsum = s->vsum;
+  a.tree = s->tree;
   a.seq = lg.seq;
   a.in_arena = s->arena[lg.in_id];
   a.in_off = s->toff[lg.in_id];
@@ -287,7 +290,7 @@ void build_args(const sv_state* s, const Logged& lg, PassArgs& a) {
       src[g] = (src[g] == -2 || src[g] == sg) ? sg : -1;
     }
     for (int g = 0; g < a.G; ++g) a.pt_src[g] = src[g] < 0 ? -1 : src[g];
-    a.pt_ok = s->dtype == SV_C128 ? 1 : 0;
+    a.pt_ok = s->dtype == SV_C128 ? 3 : 1;  // bit 0: zero blocks; bit 1: unit rows (complex128)
   }
   a.ngroups = s->nblocks >> a.h;
 }
@@ -307,15 +310,14 @@ int launch_logged(sv_state* s, const Logged& lg) {
     }
     cudaEventRecord(ev.first, s->st);
   }
-  cudaError_t e = launch_pass(a, s->dtype == SV_C64 ? 1 : 2, s->st);
+  cudaError_t e = s->compact ? launch_pass_compact(a, s->dtype == SV_C64 ? 1 : 2, s->st)
+                             : launch_pass(a, s->dtype == SV_C64 ? 1 : 2, s->st);
   if (e != cudaSuccess) return cuda_err(e);
   if (ev.first) {
     cudaEventRecord(ev.second, s->st);
     s->ev_pending.push_back(ev);
   }
-  e = launch_vsum_tree(s->vsum, s->nblocks, s->tree, s->vroot, s->sc, s->st);
-  if (e != cudaSuccess) return cuda_err(e);
-  e = launch_finalize(s->sc, s->vroot, s->two2, lg.in_id, lg.seq, s->st);
+  e = launch_norm(s->sc, s->vsum, s->nblocks, s->tree, s->two2, lg.out_id, lg.seq, s->st);
   return cuda_err(e);
 }
 
@@ -364,7 +366,9 @@ int reserve_arena(sv_state* s, int id, size_t want) {
 }
 
 int grow_arena(sv_state* s, int id, size_t need) {
-  size_t want = std::max(s->arena_r[id].bytes + s->arena_r[id].bytes / 2, need + need / 4);
+  // twice what the failed pass asked for: the passes after it (replayed next) tend to grow
+  // further, and every overflow costs a replay
+  size_t want = std::max(s->arena_r[id].bytes + s->arena_r[id].bytes / 2, 2 * need);
   region_free(s->pool, &s->arena_r[id]);
   if (!region_alloc(s->pool, &s->arena_r[id], want)) {
     if (!region_alloc(s->pool, &s->arena_r[id], need)) return SV_ERR_OOM;
@@ -474,7 +478,7 @@ int sv_create_ex(sv_pool* pool, int n, int sl, int bl, double eb, int dtype, siz
   s->qp.r = 1.0 / s->qp.two;
   s->two2 = s->qp.two * s->qp.two;
   s->nblocks = 1ull << (n - bl);
-  // metadata run: scalars | tables 0, 1 | block summaries 0, 1 | vsum | tree scratch | root
+  // metadata run: scalars | tables 0, 1 | block summaries 0, 1 | vsum | tree scratch
   const size_t nb = s->nblocks;
   size_t off = 0;
   const size_t o_sc = off;
@@ -494,9 +498,7 @@ int sv_create_ex(sv_pool* pool, int n, int sl, int bl, double eb, int dtype, siz
   const size_t o_vsum = off;
   off += round_up(nb * 8, 256);
   const size_t o_tree = off;
-  off += round_up(2 * (nb / 2048 + 1) * 8, 256);
-  const size_t o_root = off;
-  off += 256;
+  off += round_up(2 * (nb / 256 + 1) * 8, 256);
   if (!region_alloc(pool, &s->meta_r, off)) {
     delete s;
     return SV_ERR_OOM;
@@ -511,7 +513,6 @@ int sv_create_ex(sv_pool* pool, int n, int sl, int bl, double eb, int dtype, siz
   s->binfo[1] = (BlkInfo*)(m + o_info1);
   s->vsum = (double*)(m + o_vsum);
   s->tree = (double*)(m + o_tree);
-  s->vroot = (double*)(m + o_root);
   // arenas: the initial state is nearly all 16-byte CONST blocks
   const size_t init_cap = arena_bytes ? arena_bytes : std::max<size_t>(kPage, nb * 64);
   for (int id = 0; id < 2; ++id) {
@@ -599,10 +600,14 @@ int sv_sync(sv_state* s) {
     if (rc) return rc;
     if (h.status == 0) {
       s->log.clear();
-      s->sync_every = std::min(256, s->sync_every * 2);
-      // the arena the next pass writes gets room for 1.5x the current state
+      // check often while the state grows (an overflow costs a replay of every pass since
+      // the failed one), rarely once it does not
       const size_t live = (size_t)h.bump[s->cur];
-      rc = reserve_arena(s, s->cur ^ 1, live + live / 2);
+      const bool growing = live > s->last_live + s->last_live / 8;
+      s->sync_every = growing ? 1 : std::min(256, s->sync_every * 2);
+      s->last_live = live;
+      // the arena the next pass writes gets room for twice the current state
+      rc = reserve_arena(s, s->cur ^ 1, 2 * live);
       if (rc) return rc;
       for (auto& ev : s->ev_pending) {
         float ms = 0.f;
@@ -674,6 +679,12 @@ int sv_norm(sv_state* s, double* out) {
 int sv_set_threads(sv_state* s, int threads) {
   if (!s || s->plain || (threads != 0 && !threads_ok(s->b, threads))) return SV_ERR_ARG;
   s->threads = threads;
+  return SV_OK;
+}
+
+int sv_set_compact(sv_state* s, int on) {
+  if (!s || s->plain) return SV_ERR_ARG;
+  s->compact = on != 0;
   return SV_OK;
 }
 
@@ -883,7 +894,7 @@ struct sv_batch {
   Region dev_r;
   uint8_t* d_blob = nullptr;
   size_t blob_bytes = 0;
-  size_t off_prefix = 0, off_trees = 0, off_nb = 0;
+  size_t off_prefix = 0;
   uint8_t* h_buf[kRing] = {nullptr};
   cudaEvent_t h_done[kRing] = {nullptr};
   int ring = 0;
@@ -904,10 +915,6 @@ int sv_batch_create(sv_pool* pool, int max_states, void* stream, sv_batch** out)
   size_t off = (size_t)max_states * sizeof(PassArgs);
   bt->off_prefix = off;
   off += round_up((size_t)(max_states + 1) * 8, 256);
-  bt->off_trees = off;
-  off += round_up((size_t)max_states * 8, 256);
-  bt->off_nb = off;
-  off += round_up((size_t)max_states * 8, 256);
   bt->blob_bytes = off;
   if (!region_alloc(pool, &bt->dev_r, off)) {
     delete bt;
@@ -981,8 +988,6 @@ int sv_batch_apply(sv_batch* bt, sv_state* const* states, const sv_gate_t* gates
   uint8_t* hb = bt->h_buf[slot];
   PassArgs* hd = (PassArgs*)hb;
   unsigned long long* hp = (unsigned long long*)(hb + bt->off_prefix);
-  const double** ht = (const double**)(hb + bt->off_trees);
-  unsigned long long* hn = (unsigned long long*)(hb + bt->off_nb);
   std::vector<Logged> logs((size_t)count);
   int kmax = 1, gmax = 1;
   hp[0] = 0;
@@ -998,22 +1003,18 @@ int sv_batch_apply(sv_batch* bt, sv_state* const* states, const sv_gate_t* gates
     lg.out_id = s->cur ^ 1;
     build_args(s, lg, hd[i]);
     hp[i + 1] = hp[i] + hd[i].ngroups;
-    ht[i] = s->tree;
-    hn[i] = s->nblocks;
     kmax = std::max(kmax, hd[i].K);
     gmax = std::max(gmax, hd[i].G);
   }
   const int kbucket = kmax <= 2 ? 2 : (kmax <= 4 ? 4 : 8);
   const PassArgs* d_descs = (const PassArgs*)bt->d_blob;
   const unsigned long long* d_prefix = (const unsigned long long*)(bt->d_blob + bt->off_prefix);
-  const double* const* d_trees = (const double* const*)(bt->d_blob + bt->off_trees);
-  const unsigned long long* d_nb = (const unsigned long long*)(bt->d_blob + bt->off_nb);
   auto enqueue = [&](uint8_t* src) -> cudaError_t {
     cudaError_t r = cudaMemcpyAsync(bt->d_blob, src, bt->blob_bytes, cudaMemcpyHostToDevice, bt->st);
     if (r == cudaSuccess)
       r = launch_pass_batch(d_descs, d_prefix, count, hp[count], s0->b, gmax, kbucket,
                             s0->dtype == SV_C64 ? 1 : 2, s0->threads, bt->st);
-    if (r == cudaSuccess) r = launch_norm_batch(d_descs, d_trees, d_nb, count, bt->st);
+    if (r == cudaSuccess) r = launch_norm_batch(d_descs, count, bt->st);
     return r;
   };
   GraphKey key{count, kbucket, gmax, hp[count]};

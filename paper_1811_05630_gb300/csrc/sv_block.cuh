@@ -72,11 +72,13 @@ struct __align__(16) PassArgs {
   unsigned int* out_len;
   DevScalars* sc;
   double* vsum;
+  double* tree;  // scratch of the norm kernel's verbatim-sum tree (2 (nblocks / 256 + 1) doubles)
   unsigned int seq;
-  // stream pass-through (complex128): block slot g of a group whose high controls are all 1
-  // takes the codes of slot pt_src[g] unchanged (-1: never); need[g] is the mask of the
-  // slots its outputs read
   int threads;  // CTA size (0: worker_threads(b)); results do not depend on it
+  // stream pass-through: pt_ok bit 0 re-emits blocks whose inputs are all zero, bit 1
+  // (complex128) blocks whose rows are unit rows: slot g of a group whose high controls are
+  // all 1 takes the codes of slot pt_src[g] (-1: never); need[g] is the mask of the slots
+  // its outputs read
   int pt_ok;
   int pt_src[4];
   unsigned int need[4];
@@ -775,35 +777,84 @@ __device__ void Worker<Real>::encode(int g, unsigned long long blk, const PassAr
     nverb = nverb_raw < kVmax ? nverb_raw : kVmax;
   }
   const int C = nv / kChunk;
-  // ---- pass 1: statistics over this thread's values ----
+  // ---- pass 1: statistics and the symbol histogram over this thread's values ----
+  // (hash table; runs of equal symbols merged before an insert; inserts stop once the block
+  // has more distinct symbols than Huffman mode takes)
+  for (int i = tid; i < L.hs; i += T) {
+    hkey[i] = kEmpty;
+    hval[i] = 0;
+  }
+  if (tid == 0) {
+    m->D = 0;
+    m->cnt = 0;
+  }
+  __syncthreads();
   const int j0 = tid * vpt;
   const int32_t q0 = qb[0], q1 = qb[1];
-  int32_t pr = j0 >= 2 ? code(g, j0 - 2) : 0, pi = j0 >= 2 ? code(g, j0 - 1) : 0;
-  unsigned long long sqh = 0, sql = 0;
-  uint32_t zmax = 0, amax = 0;
-  int nesc = 0;
-  bool cst = true;
-#pragma unroll 4
-  for (int i = 0; i < vpt; ++i) {
-    const int j = j0 + i;
-    const int32_t c = code(g, j);
-    const int32_t p = (j & 1) ? pi : pr;
-    const int32_t d = c - p;
-    if (j & 1) pi = c;
-    else pr = c;
-    const uint64_t s2 = (uint64_t)((int64_t)c * (int64_t)c);
-    sqh += s2 >> 32;
-    sql += s2 & 0xffffffffull;
-    const uint32_t z = zigzag(d);
-    zmax = z > zmax ? z : zmax;
-    const uint32_t ac = (uint32_t)(c < 0 ? -c : c);
-    amax = ac > amax ? ac : amax;
-    nesc += (d < -kRadius || d > kRadius) ? 1 : 0;
-    cst = cst && (c == ((j & 1) ? q1 : q0));
+  BlkStats bs;
+  bs.sqh = bs.sql = 0;
+  bs.zmax = bs.amax = 0;
+  bs.nesc = 0;
+  bs.cst = 1;
+  {
+    int32_t pr = j0 >= 2 ? code(g, j0 - 2) : 0, pi = j0 >= 2 ? code(g, j0 - 1) : 0;
+    uint32_t run_sym = 0xFFFFFFFFu, run = 0;
+    for (int i = 0; i <= vpt; ++i) {
+      uint32_t sym = 0xFFFFFFFEu;
+      if (i < vpt) {
+        const int j = j0 + i;
+        const int32_t c = code(g, j);
+        const int32_t d = c - ((j & 1) ? pi : pr);
+        if (j & 1) pi = c;
+        else pr = c;
+        const uint64_t s2 = (uint64_t)((int64_t)c * (int64_t)c);
+        bs.sqh += s2 >> 32;
+        bs.sql += s2 & 0xffffffffull;
+        const uint32_t z = zigzag(d);
+        bs.zmax = z > bs.zmax ? z : bs.zmax;
+        const uint32_t ac = (uint32_t)(c < 0 ? -c : c);
+        bs.amax = ac > bs.amax ? ac : bs.amax;
+        const bool esc = d < -kRadius || d > kRadius;
+        bs.nesc += esc ? 1 : 0;
+        bs.cst &= (c == ((j & 1) ? q1 : q0)) ? 1 : 0;
+        sym = esc ? 0u : (uint32_t)(d + 32768);
+      }
+      if (sym == run_sym) {
+        run++;
+        continue;
+      }
+      if (run && *(volatile int*)&m->D <= kHuffMaxD) {
+        uint32_t hslot = hash_sym(run_sym) & (uint32_t)(L.hs - 1);
+        for (int probe = 0; probe < L.hs; ++probe) {
+          const uint32_t k = hkey[hslot];
+          if (k == run_sym) {
+            atomicAdd(&hval[hslot], run);
+            break;
+          }
+          if (k == kEmpty) {
+            const uint32_t old = atomicCAS(&hkey[hslot], kEmpty, run_sym);
+            if (old == kEmpty) {
+              atomicAdd(&m->D, 1);
+              atomicAdd(&hval[hslot], run);
+              break;
+            }
+            if (old == run_sym) {
+              atomicAdd(&hval[hslot], run);
+              break;
+            }
+          }
+          hslot = (hslot + 1) & (uint32_t)(L.hs - 1);
+        }
+      }
+      run_sym = sym;
+      run = 1;
+    }
   }
-  const bool is_const = __syncthreads_and(cst) && nverb_raw == 0;
-  const unsigned long long Sh = block_reduce_sum_u64(sqh, m->red);
-  const unsigned long long Sl = block_reduce_sum_u64(sql, m->red);
+  block_reduce_stats(bs, (BlkStats*)m->red);  // syncs: the histogram is complete after it
+  const bool is_const = bs.cst && nverb_raw == 0;
+  const unsigned long long Sh = bs.sqh, Sl = bs.sql;
+  uint32_t amax = bs.amax;
+  const int nesc_blk = bs.nesc;
   int mode = kModeConst, lmax = 0, width = 0, D = 0;
   uint32_t pbits = 0, body = 0;
   uint32_t* keys = (uint32_t*)build;
@@ -816,68 +867,10 @@ __device__ void Worker<Real>::encode(int g, unsigned long long blk, const PassAr
   uint32_t* tsk = (uint32_t*)(build + L.sort_off);  // rank-sort scratch
   uint32_t* tsv = tsk + L.sort_n;
   if (!is_const) {
-    block_reduce_max2_u32(zmax, amax, m->scan);
-    width = bit_width(zmax);
+    width = bit_width(bs.zmax);
     const uint32_t pack_body = 4u * (((uint32_t)nv * (uint32_t)width + 31u) / 32u);
-    // ---- histogram into the hash table (runs of equal symbols merged first) ----
-    for (int i = tid; i < L.hs; i += T) {
-      hkey[i] = kEmpty;
-      hval[i] = 0;
-    }
-    if (tid == 0) {
-      m->D = 0;
-      m->nesc = 0;
-      m->cnt = 0;
-    }
-    __syncthreads();
-    atomicAdd(&m->nesc, nesc);
-    {
-      int32_t pr2 = j0 >= 2 ? code(g, j0 - 2) : 0, pi2 = j0 >= 2 ? code(g, j0 - 1) : 0;
-      uint32_t run_sym = 0xFFFFFFFFu, run = 0;
-      for (int i = 0; i <= vpt; ++i) {
-        uint32_t sym = 0xFFFFFFFEu;
-        if (i < vpt) {
-          const int j = j0 + i;
-          const int32_t c = code(g, j);
-          const int32_t d = c - ((j & 1) ? pi2 : pr2);
-          if (j & 1) pi2 = c;
-          else pr2 = c;
-          sym = (d < -kRadius || d > kRadius) ? 0u : (uint32_t)(d + 32768);
-        }
-        if (sym == run_sym) {
-          run++;
-          continue;
-        }
-        if (run && *(volatile int*)&m->D <= kHuffMaxD) {
-          uint32_t hslot = hash_sym(run_sym) & (uint32_t)(L.hs - 1);
-          for (int probe = 0; probe < L.hs; ++probe) {
-            const uint32_t k = hkey[hslot];
-            if (k == run_sym) {
-              atomicAdd(&hval[hslot], run);
-              break;
-            }
-            if (k == kEmpty) {
-              const uint32_t old = atomicCAS(&hkey[hslot], kEmpty, run_sym);
-              if (old == kEmpty) {
-                atomicAdd(&m->D, 1);
-                atomicAdd(&hval[hslot], run);
-                break;
-              }
-              if (old == run_sym) {
-                atomicAdd(&hval[hslot], run);
-                break;
-              }
-            }
-            hslot = (hslot + 1) & (uint32_t)(L.hs - 1);
-          }
-        }
-        run_sym = sym;
-        run = 1;
-      }
-    }
-    __syncthreads();
     D = m->D;
-    const int ne = m->nesc;
+    const int ne = nesc_blk;
     bool use_huff = false;
     if (D <= L.dcap && D <= kHuffMaxD) {
       const int P2 = next_pow2(D);
@@ -992,10 +985,15 @@ __device__ void Worker<Real>::encode(int g, unsigned long long blk, const PassAr
         const uint32_t off_pay = off_chunk + (uint32_t)pad_to(2 * C, 4);
         for (int l = tid + 1; l <= lmax; l += T) st16[kHdr / 2 + l - 1] = (uint16_t)m->lcount[l];
         for (int i = tid; i < D; i += T) st16[off_sym / 2 + i] = (uint16_t)(keys[i] & 0xFFFFu);
-        // pass 2: bits per thread, then positions
+        // pass 2: bits per thread, then positions. Without escapes (and without complex64
+        // verbatim values, whose raw bits live in the code slots) each value's code word
+        // replaces its code in place, so the bit writer needs no second lookup.
+        const bool keep_cw = nesc_blk == 0 && (!kMask || nverb_raw == 0);
         uint32_t nb = 0;
         {
           int32_t pr2 = j0 >= 2 ? code(g, j0 - 2) : 0, pi2 = j0 >= 2 ? code(g, j0 - 1) : 0;
+          __syncthreads();  // every thread has its two preceding codes before any slot is rewritten
+          int32_t* qw = q + g * nv;
           for (int i = 0; i < vpt; ++i) {
             const int j = j0 + i;
             const int32_t c = code(g, j);
@@ -1004,7 +1002,9 @@ __device__ void Worker<Real>::encode(int g, unsigned long long blk, const PassAr
             else pr2 = c;
             const uint32_t sym = (d < -kRadius || d > kRadius) ? 0u : (uint32_t)(d + 32768);
             const uint32_t hs_ = find_slot(sym);
-            nb += (hs_ < (uint32_t)L.hs ? (hval[hs_] & 31u) : 0u) + (sym == 0 ? 32u : 0u);
+            const uint32_t cl = hs_ < (uint32_t)L.hs ? hval[hs_] : 0u;
+            nb += (cl & 31u) + (sym == 0 ? 32u : 0u);
+            if (keep_cw) qw[j] = (int32_t)cl;
           }
         }
         uint32_t tot = 0;
@@ -1021,7 +1021,13 @@ __device__ void Worker<Real>::encode(int g, unsigned long long blk, const PassAr
         pay = stage + off_pay / 4;
         BitWriter bw;
         bw.start(pay, start);
-        {
+        if (keep_cw) {
+          const uint32_t* cw = (const uint32_t*)(q + g * nv) + j0;
+          for (int i = 0; i < vpt; ++i) {
+            const uint32_t cl = cw[i];
+            bw.put(cl >> 5, (int)(cl & 31u));
+          }
+        } else {
           int32_t pr2 = j0 >= 2 ? code(g, j0 - 2) : 0, pi2 = j0 >= 2 ? code(g, j0 - 1) : 0;
           for (int i = 0; i < vpt; ++i) {
             const int j = j0 + i;
@@ -1105,7 +1111,7 @@ __device__ void Worker<Real>::encode(int g, unsigned long long blk, const PassAr
     const unsigned long long c1 = (old + lo < old) ? 1ull : 0ull;
     if (hi + c1) atomicAdd(&a.sc->acc.sq_hi, hi + c1);
     if (nverb) atomicAdd(&a.sc->acc.n_verbatim, (unsigned long long)nverb);
-    if (mode != kModeConst) atomicAdd(&a.sc->acc.n_escape, (unsigned long long)m->nesc);
+    if (mode != kModeConst) atomicAdd(&a.sc->acc.n_escape, (unsigned long long)nesc_blk);
     atomicAdd(&a.sc->acc.modes[mode], 1ull);
     if (a.out_info) {
       if (is_const) {
@@ -1114,7 +1120,7 @@ __device__ void Worker<Real>::encode(int g, unsigned long long blk, const PassAr
       }
       BlkInfo bi;
       bi.sq_lo = lo;
-      bi.sq_hi_nesc = (unsigned int)(hi & 0xFFull) | ((unsigned int)(mode != kModeConst ? m->nesc : 0) << 8);
+      bi.sq_hi_nesc = (unsigned int)(hi & 0xFFull) | ((unsigned int)(mode != kModeConst ? nesc_blk : 0) << 8);
       bi.maxq_mode = (amax & 0x1FFFFFFFu) | ((unsigned int)mode << 29) | (nverb_raw ? 0x80000000u : 0u);
       a.out_info[blk] = bi;
     }

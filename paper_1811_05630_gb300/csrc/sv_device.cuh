@@ -196,27 +196,40 @@ __device__ __forceinline__ T block_reduce_max(T v, T* ws) {
   return r;
 }
 
-// Two block-wide maxima with one pair of barriers (ws: 2 words per warp).
-__device__ __forceinline__ void block_reduce_max2_u32(uint32_t& a, uint32_t& b, uint32_t* ws) {
+// Per-block statistics of a code block, reduced across the CTA with one pair of barriers:
+// sums of the high/low 32-bit halves of q^2 and of escapes, maxima of zigzag(delta) and |q|,
+// AND of the constant-block test. ws: one entry per warp (at most 8).
+struct BlkStats {
+  unsigned long long sqh, sql;
+  uint32_t zmax, amax;
+  int nesc, cst;
+};
+
+__device__ __forceinline__ void block_reduce_stats(BlkStats& v, BlkStats* ws) {
   for (int o = 16; o > 0; o >>= 1) {
-    const uint32_t ya = __shfl_xor_sync(0xffffffffu, a, o), yb = __shfl_xor_sync(0xffffffffu, b, o);
-    a = a > ya ? a : ya;
-    b = b > yb ? b : yb;
+    v.sqh += __shfl_xor_sync(0xffffffffu, v.sqh, o);
+    v.sql += __shfl_xor_sync(0xffffffffu, v.sql, o);
+    const uint32_t z = __shfl_xor_sync(0xffffffffu, v.zmax, o), a = __shfl_xor_sync(0xffffffffu, v.amax, o);
+    v.zmax = z > v.zmax ? z : v.zmax;
+    v.amax = a > v.amax ? a : v.amax;
+    v.nesc += __shfl_xor_sync(0xffffffffu, v.nesc, o);
+    v.cst &= __shfl_xor_sync(0xffffffffu, v.cst, o);
   }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-  if (lane == 0) {
-    ws[2 * wid] = a;
-    ws[2 * wid + 1] = b;
+  if (lane == 0) ws[wid] = v;
+  __syncthreads();
+  BlkStats r = ws[0];
+  for (int w = 1; w < nw; ++w) {
+    const BlkStats& x = ws[w];
+    r.sqh += x.sqh;
+    r.sql += x.sql;
+    r.zmax = x.zmax > r.zmax ? x.zmax : r.zmax;
+    r.amax = x.amax > r.amax ? x.amax : r.amax;
+    r.nesc += x.nesc;
+    r.cst &= x.cst;
   }
   __syncthreads();
-  uint32_t ra = 0, rb = 0;
-  for (int w = 0; w < nw; ++w) {
-    ra = ws[2 * w] > ra ? ws[2 * w] : ra;
-    rb = ws[2 * w + 1] > rb ? ws[2 * w + 1] : rb;
-  }
-  __syncthreads();
-  a = ra;
-  b = rb;
+  v = r;
 }
 
 __device__ __forceinline__ unsigned long long block_reduce_sum_u64(unsigned long long v,

@@ -9,19 +9,17 @@ namespace sv {
 
 // Fused gate pass (Algorithm 1 over every slice) for one state; Real by dtype (1 = float).
 cudaError_t launch_pass(const PassArgs& a, int dtype, cudaStream_t st);
-// The fused pass over the block-groups of many states (one descriptor each), and the
-// batched norm finalization (verbatim-sum tree per state in one CTA, then N and sigma).
+// The same pass built with a register cap for 1- and 2-qubit gates (others: launch_pass).
+cudaError_t launch_pass_compact(const PassArgs& a, int dtype, cudaStream_t st);
+// The fused pass over the block-groups of many states (one descriptor each).
 cudaError_t launch_pass_batch(const PassArgs* descs, const unsigned long long* gprefix, int nstates,
                               unsigned long long total_groups, int b, int Gmax, int Kmax, int dtype,
                               int threads, cudaStream_t st);
-cudaError_t launch_norm_batch(const PassArgs* descs, const double* const* trees, const unsigned long long* nblocks,
-                              int nstates, cudaStream_t st);
-// Pairwise (level by level) sum of n = 2^k per-block verbatim sums into root[0].
-cudaError_t launch_vsum_tree(const double* vsum, unsigned long long n, double* scratch,
-                             double* root, const DevScalars* sc, cudaStream_t st);
-// N, sigma, statistics; resets the accumulators and the bump of arena `reset_id`.
-cudaError_t launch_finalize(DevScalars* sc, const double* root, double two2, int reset_id,
-                            unsigned int seq, cudaStream_t st);
+// Norm finalization after a pass (one CTA per state): verbatim-sum tree when needed, N, sigma,
+// statistics; resets the bump of the arena the next pass writes.
+cudaError_t launch_norm(DevScalars* sc, const double* vsum, unsigned long long nb, double* tree, double two2,
+                        int out_id, unsigned int seq, cudaStream_t st);
+cudaError_t launch_norm_batch(const PassArgs* descs, int nstates, cudaStream_t st);
 
 // Standalone codec.
 cudaError_t launch_codec_compress(const void* values, unsigned long long nblocks, int b,

@@ -1,0 +1,476 @@
+// sv_pass.cuh — the fused gate pass (Algorithm 1 of Wu et al., PMES 2018): gate arithmetic,
+// the complex128 fixed-point path, stream pass-through and the k_pass kernel. Included by the
+// translation units that instantiate k_pass (with and without a register cap).
+#pragma once
+#include "sv_internal.h"
+
+namespace sv {
+
+template <typename Real>
+struct Arith;
+template <>
+struct Arith<double> {
+  __device__ static double mul(double a, double b) { return __dmul_rn(a, b); }
+  __device__ static double add(double a, double b) { return __dadd_rn(a, b); }
+  __device__ static double sub(double a, double b) { return __dsub_rn(a, b); }
+};
+template <>
+struct Arith<float> {
+  __device__ static float mul(float a, float b) { return __fmul_rn(a, b); }
+  __device__ static float add(float a, float b) { return __fadd_rn(a, b); }
+  __device__ static float sub(float a, float b) { return __fsub_rn(a, b); }
+};
+
+template <typename Real>
+__device__ __forceinline__ Real gate_coef(const PassArgs& a, int e);
+template <>
+__device__ __forceinline__ double gate_coef<double>(const PassArgs& a, int e) { return a.g[e]; }
+template <>
+__device__ __forceinline__ float gate_coef<float>(const PassArgs& a, int e) { return a.gf[e]; }
+
+__device__ __forceinline__ unsigned long long insert_zero_bit(unsigned long long v, int p) {
+  return ((v >> p) << (p + 1)) | (v & ((1ull << p) - 1ull));
+}
+
+// ---------------------------------------------------------------------------------------
+// complex128 fast path. The exact step chain of a pass (x' = fl(q 2eb), y = fl(sigma x'),
+// z = ordered sum of fl products, t = fl(z r), q' = rint(t)) lands within 2^-48 R Q of the
+// real number T = sum c q with c = sigma G (2eb r) (R: largest row sum of |c|, Q = 2^29 the
+// code limit). W below is T in fixed point with error at most 3 2^-F. Where W is farther
+// than the sum of both bounds (plus 2^-21 for the verbatim test) from a rounding tie and
+// inside the code range, rint(t) = round(W) and the value is not verbatim; otherwise that
+// component is recomputed with the exact step chain. Results are identical either way.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ int ceil_log2(double x) {
+  const int e = ilogb(x);  // 2^e <= x < 2^(e+1)
+  return scalbn(1.0, e) == x ? e : e + 1;
+}
+
+__device__ inline void fast_prepare(FastGate* fg, const PassArgs& a, double sigma) {
+  const double s1 = __dmul_rn(a.use_sigma ? sigma : 1.0, a.two_r);
+  const int K = a.K;
+  double R = fabs(s1);
+  if (a.apply_gate) {
+    for (int jj = 0; jj < K; ++jj) {
+      double row = 0.0;
+      for (int m = 0; m < K; ++m)
+        row += fabs(__dmul_rn(a.g[2 * (jj * K + m)], s1)) + fabs(__dmul_rn(a.g[2 * (jj * K + m) + 1], s1));
+      R = row > R ? row : R;
+    }
+  }
+  const int cl = R > 0.0 ? ceil_log2(R) : 0;
+  int F = 30 - (cl > 0 ? cl : 0);
+  if (!(R > 0.0) || cl > 16 || !isfinite(R)) F = -1;  // fast path off
+  fg->F = F;
+  if (F < 0) return;
+  fg->margin = (long long)ceil(R * scalbn(1.0, F - 19)) + 3 + (1ll << (F > 21 ? F - 21 : 0));
+  const double scale = scalbn(1.0, F + 31);
+  auto fix = [&](double c, int32_t* hi, int32_t* lo) {
+    const long long v = __double2ll_rn(__dmul_rn(c, scale));
+    *hi = (int32_t)(v >> 31);
+    *lo = (int32_t)(v & 0x7fffffffll);
+  };
+  fix(s1, &fg->idhi, &fg->idlo);
+  // |q| <= qsafe gives rint of the exact chain for q * s1 equal to q: |q| |s1' - 1| plus the
+  // chain's error (<= 2^-19 R here) stays below 1/2 - 2^-18 (s1' the exact scale, within
+  // 2^-51 of s1)
+  {
+    const double dev = fabs(s1 - 1.0) + scalbn(1.0, -50);
+    const double lim = (0.5 - scalbn(1.0, -18) - R * scalbn(1.0, -19)) / dev;
+    fg->qsafe = lim >= 536870000.0 ? 536870000 : (lim > 0.0 ? (int)lim : -1);
+  }
+  for (int jj = 0; jj < 8; ++jj)
+    for (int p = 0; p < 2; ++p) {
+      fg->ssrc[jj][p] = -1;
+      fg->ssgn[jj][p] = 1;
+    }
+  if (!a.apply_gate) return;
+  for (int jj = 0; jj < K; ++jj) {
+    int nz = 0, mz = -1;
+    for (int m = 0; m < K; ++m)
+      if (a.g[2 * (jj * K + m)] != 0.0 || a.g[2 * (jj * K + m) + 1] != 0.0) {
+        ++nz;
+        mz = m;
+      }
+    if (nz != 1) continue;
+    const double gr = a.g[2 * (jj * K + mz)], gi = a.g[2 * (jj * K + mz) + 1];
+    if (gi == 0.0 && (gr == 1.0 || gr == -1.0)) {  // (+-1) (x + iy)
+      const int sg = gr > 0 ? 1 : -1;
+      fg->ssrc[jj][0] = (int8_t)(2 * mz);
+      fg->ssgn[jj][0] = (int8_t)sg;
+      fg->ssrc[jj][1] = (int8_t)(2 * mz + 1);
+      fg->ssgn[jj][1] = (int8_t)sg;
+    } else if (gr == 0.0 && (gi == 1.0 || gi == -1.0)) {  // (+-i) (x + iy) = -+y +- ix
+      const int sg = gi > 0 ? 1 : -1;
+      fg->ssrc[jj][0] = (int8_t)(2 * mz + 1);
+      fg->ssgn[jj][0] = (int8_t)-sg;
+      fg->ssrc[jj][1] = (int8_t)(2 * mz);
+      fg->ssgn[jj][1] = (int8_t)sg;
+    }
+  }
+  int diag = 1;
+  for (int jj = 0; jj < K; ++jj)
+    for (int m = 0; m < K; ++m) {
+      const double A = __dmul_rn(a.g[2 * (jj * K + m)], s1);
+      const double Bc = __dmul_rn(a.g[2 * (jj * K + m) + 1], s1);
+      if (m != jj && (A != 0.0 || Bc != 0.0)) diag = 0;
+      // re += A q_re - B q_im ; im += B q_re + A q_im
+      fix(A, &fg->chi[jj][0][m][0], &fg->clo[jj][0][m][0]);
+      fix(-Bc, &fg->chi[jj][0][m][1], &fg->clo[jj][0][m][1]);
+      fix(Bc, &fg->chi[jj][1][m][0], &fg->clo[jj][1][m][0]);
+      fix(A, &fg->chi[jj][1][m][1], &fg->clo[jj][1][m][1]);
+    }
+  fg->diag = diag;
+}
+
+// round(W / 2^F) when it provably equals the exact chain's code; false otherwise
+__device__ __forceinline__ bool fast_round(long long W, int F, long long margin, int32_t* q) {
+  const long long half = 1ll << (F - 1);
+  const long long qn = (W + half) >> F;
+  const long long frac = W - (qn << F);
+  if (frac < margin - half || frac >= half - margin) return false;
+  if (qn >= (1ll << 29) - 1 || qn <= -((1ll << 29) - 1)) return false;
+  *q = (int32_t)qn;
+  return true;
+}
+
+// the exact step chain for one output component of a tuple (no verbatim input)
+__device__ __forceinline__ double exact_component(const PassArgs& a, double sigma, const int32_t* qv,
+                                                  int jj, int p, bool ctrl) {
+  if (!ctrl) {
+    const double x = __dmul_rn((double)qv[2 * jj + p], a.qp.two);
+    return a.use_sigma ? __dmul_rn(sigma, x) : x;
+  }
+  double ar = 0.0, ai = 0.0;
+  for (int m = 0; m < a.K; ++m) {
+    double yr = __dmul_rn((double)qv[2 * m], a.qp.two), yi = __dmul_rn((double)qv[2 * m + 1], a.qp.two);
+    if (a.use_sigma) {
+      yr = __dmul_rn(sigma, yr);
+      yi = __dmul_rn(sigma, yi);
+    }
+    const double gr = a.g[2 * (jj * a.K + m)], gi = a.g[2 * (jj * a.K + m) + 1];
+    const double pr = __dsub_rn(__dmul_rn(gr, yr), __dmul_rn(gi, yi));
+    const double pi = __dadd_rn(__dmul_rn(gr, yi), __dmul_rn(gi, yr));
+    if (m == 0) {
+      ar = pr;
+      ai = pi;
+    } else {
+      ar = __dadd_rn(ar, pr);
+      ai = __dadd_rn(ai, pi);
+    }
+  }
+  return p ? ai : ar;
+}
+
+// One tuple through the exact step chain in the value type (verbatim inputs; complex64).
+template <typename Real, int KM>
+__device__ __forceinline__ void tuple_exact(Worker<Real>& w, const PassArgs& a, Real sg, int bp, bool ctrl) {
+  using A = Arith<Real>;
+  const Layout& L = w.L;
+  Real yr[KM], yi[KM];
+  int gs[KM], js[KM];
+#pragma unroll
+  for (int mm = 0; mm < KM; ++mm) {
+    if (mm < a.K) {
+      const int p = bp + a.pos_delta[mm];
+      const int g = p / L.nv;
+      const int j = p - g * L.nv;
+      gs[mm] = g;
+      js[mm] = j;
+      const Real xr = w.value_at(g, j), xi = w.value_at(g, j + 1);
+      yr[mm] = a.use_sigma ? A::mul(sg, xr) : xr;
+      yi[mm] = a.use_sigma ? A::mul(sg, xi) : xi;
+    }
+  }
+  if (ctrl) {
+    Real zr[KM], zi[KM];
+#pragma unroll
+    for (int jj = 0; jj < KM; ++jj) {
+      if (jj < a.K) {
+        Real ar = 0, ai = 0;
+#pragma unroll
+        for (int mm = 0; mm < KM; ++mm) {
+          if (mm < a.K) {
+            const Real gr = gate_coef<Real>(a, 2 * (jj * a.K + mm));
+            const Real gi = gate_coef<Real>(a, 2 * (jj * a.K + mm) + 1);
+            const Real pr = A::sub(A::mul(gr, yr[mm]), A::mul(gi, yi[mm]));
+            const Real pi = A::add(A::mul(gr, yi[mm]), A::mul(gi, yr[mm]));
+            if (mm == 0) {
+              ar = pr;
+              ai = pi;
+            } else {
+              ar = A::add(ar, pr);
+              ai = A::add(ai, pi);
+            }
+          }
+        }
+        zr[jj] = ar;
+        zi[jj] = ai;
+      }
+    }
+#pragma unroll
+    for (int mm = 0; mm < KM; ++mm)
+      if (mm < a.K) {
+        yr[mm] = zr[mm];
+        yi[mm] = zi[mm];
+      }
+  }
+#pragma unroll
+  for (int mm = 0; mm < KM; ++mm)
+    if (mm < a.K) {
+      w.put_value(gs[mm], js[mm], yr[mm]);
+      w.put_value(gs[mm], js[mm] + 1, yi[mm]);
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Algorithm 1: for the gate G, for every slice: Decompress, Normalize, GateComputation,
+// Compress. One CTA per group of 2^h coupled blocks (grid-stride over the groups).
+// ---------------------------------------------------------------------------------------
+// One group of 2^h coupled blocks of one state: Decompress, Normalize + GateComputation,
+// Compress (shared by the single-state and the batched pass kernels).
+template <typename Real, int KM>
+__device__ __forceinline__ void pass_group(Worker<Real>& w, const PassArgs& a, const FastGate* fg,
+                                           double sigma, unsigned long long grp) {
+  using A = Arith<Real>;
+  const Layout& L = w.L;
+  const Real sg = (Real)sigma;  // complex64: sigma rounded to float once
+  const int B = L.nv / 2;
+  constexpr bool kFast = sizeof(Real) == 8;
+  unsigned long long base = grp;
+  for (int l = 0; l < a.h; ++l) base = insert_zero_bit(base, a.high_pos[l]);
+  unsigned long long blks[4];
+  for (int g = 0; g < a.G; ++g) {
+    unsigned long long bid = base;
+    for (int l = 0; l < a.h; ++l)
+      if ((g >> l) & 1) bid |= 1ull << a.slot_shift[l];
+    blks[g] = bid;
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) w.vout_cnt[threadIdx.x] = 0;
+  // ---- stream pass-through ----
+  // complex128: block slot g keeps the codes of slot src (src = g where the gate acts as the identity on
+  // it: the group's high controls are not all 1, or its rows are unit rows; another slot for
+  // a +1 permutation across blocks) when that slot holds no verbatim value and every |q| is
+  // within qsafe: then each output code equals its input code exactly (the same argument as
+  // the single-term shortcut below), and the block's stream is the source stream.
+  // A block whose inputs (the blocks it reads) are all zero codes with no verbatim value
+  // has zero outputs under any gate (every step of the chain maps 0 to 0): it keeps its
+  // own all-zero stream, in either precision.
+  bool any_pt = false;
+  if (a.pt_ok) {
+    if (threadIdx.x == 0) {
+      const bool hc = ((blks[0] << a.b) & a.cmask_high) == a.cmask_high;
+      const bool unit_rule = kFast && (a.pt_ok & 2) && fg->F >= 0;
+      unsigned int dmask = 0;
+      int npt = 0;
+      for (int g = 0; g < a.G; ++g) {
+        const unsigned int reads = hc ? a.need[g] : (1u << g);
+        int src = -1;
+        if (unit_rule) {
+          const int c = hc ? a.pt_src[g] : g;
+          if (c >= 0) {
+            const unsigned int mm = a.in_info[blks[c]].maxq_mode;
+            if (!(mm & 0x80000000u) && (long long)(mm & 0x1FFFFFFFu) <= (long long)fg->qsafe) src = c;
+          }
+        }
+        if (src < 0) {
+          bool zero = true;
+          for (int h = 0; h < a.G; ++h)
+            if (((reads >> h) & 1u) && (a.in_info[blks[h]].maxq_mode & 0x9FFFFFFFu)) zero = false;
+          if (zero) src = g;
+        }
+        w.m->pt[g] = src;
+        if (src >= 0) ++npt;
+        else dmask |= reads;
+      }
+      w.m->dmask = dmask;
+      w.m->npt = npt;
+    }
+    __syncthreads();
+    any_pt = w.m->npt > 0;
+    if (w.m->npt == a.G) {
+      for (int g = 0; g < a.G; ++g) w.pass_through(blks[w.m->pt[g]], blks[g], a);
+      return;
+    }
+  }
+  // ---- Decompress(S) ----
+  for (int g = 0; g < a.G; ++g) {
+    if (a.input_basis) {
+      const int pos = ((a.basis >> a.b) == blks[g]) ? 2 * (int)(a.basis & (unsigned long long)(B - 1)) : -1;
+      w.load_basis(g, pos);
+    } else if (any_pt && !((w.m->dmask >> g) & 1u)) {
+      w.load_basis(g, -1);  // read by no recoded block: zeros
+    } else {
+      w.decode(g, a.in_arena + a.in_off[blks[g]], a.in_len[blks[g]]);
+    }
+  }
+  // ---- Normalize(S) and GateComputation(G, S), tuple by tuple, in place ----
+  const int ntup = B >> a.nlow;
+  for (int u = threadIdx.x; u < ntup; u += blockDim.x) {
+    unsigned long long o = (unsigned long long)u;
+    for (int l = 0; l < a.nlow; ++l) o = insert_zero_bit(o, a.low_t[l]);
+    const unsigned long long gidx = (blks[0] << a.b) | o;
+    const bool ctrl = a.apply_gate && ((gidx & a.cmask) == a.cmask);
+    const int bp = 2 * (int)o;
+    if (kFast && fg->F >= 0) {
+      int32_t qv[2 * KM];
+      int gq[KM], jq[KM];
+      bool sentinel = false;
+#pragma unroll
+      for (int mm = 0; mm < KM; ++mm)
+        if (mm < a.K) {
+          const int p = bp + a.pos_delta[mm];
+          gq[mm] = p / L.nv;
+          jq[mm] = p - gq[mm] * L.nv;
+          qv[2 * mm] = w.q[p];
+          qv[2 * mm + 1] = w.q[p + 1];
+          sentinel |= qv[2 * mm] == kSentinel || qv[2 * mm + 1] == kSentinel;
+        }
+      if (!sentinel) {
+        const int F = fg->F;
+        const long long margin = fg->margin;
+        int32_t out[2 * KM];
+        unsigned int exact_mask = 0;
+#pragma unroll
+        for (int jj = 0; jj < KM; ++jj)
+          if (jj < a.K) {
+#pragma unroll
+            for (int p = 0; p < 2; ++p) {
+              // outputs that are +-1 times one input: exact without arithmetic when small
+              const int ssrc = ctrl ? fg->ssrc[jj][p] : 2 * jj + p;
+              bool done = false;
+              if (ssrc >= 0) {
+                int32_t qq = 0;
+#pragma unroll
+                for (int e = 0; e < 2 * KM; ++e)
+                  if (e == ssrc) qq = qv[e];
+                if ((qq < 0 ? -qq : qq) <= fg->qsafe) {
+                  out[2 * jj + p] = (ctrl && fg->ssgn[jj][p] < 0) ? -qq : qq;
+                  done = true;
+                }
+              }
+              if (!done) {
+                long long sh = 0, sl = 0;
+                if (ctrl && fg->diag) {
+  #pragma unroll
+                  for (int c = 0; c < 2; ++c) {
+                    const long long qq = qv[2 * jj + c];
+                    sh += qq * fg->chi[jj][p][jj][c];
+                    sl += (qq * fg->clo[jj][p][jj][c]) >> 4;
+                  }
+                } else if (ctrl) {
+  #pragma unroll
+                  for (int m = 0; m < KM; ++m)
+                    if (m < a.K) {
+  #pragma unroll
+                      for (int c = 0; c < 2; ++c) {
+                        const long long qq = qv[2 * m + c];
+                        sh += qq * fg->chi[jj][p][m][c];
+                        sl += (qq * fg->clo[jj][p][m][c]) >> 4;
+                      }
+                    }
+                } else {
+                  const long long qq = qv[2 * jj + p];
+                  sh = qq * fg->idhi;
+                  sl = (qq * fg->idlo) >> 4;
+                }
+                if (!fast_round(sh + (sl >> 27), F, margin, &out[2 * jj + p])) exact_mask |= 1u << (2 * jj + p);
+              }
+            }
+          }
+        double zx[2 * KM];
+        if (exact_mask) {
+#pragma unroll
+          for (int e = 0; e < 2 * KM; ++e)
+            if ((exact_mask >> e) & 1u) zx[e] = exact_component(a, sigma, qv, e >> 1, e & 1, ctrl);
+        }
+#pragma unroll
+        for (int mm = 0; mm < KM; ++mm)
+          if (mm < a.K) {
+#pragma unroll
+            for (int p = 0; p < 2; ++p) {
+              const int e = 2 * mm + p;
+              if ((exact_mask >> e) & 1u) w.put_value(gq[mm], jq[mm] + p, (Real)zx[e]);
+              else w.q[gq[mm] * L.nv + jq[mm] + p] = out[e];
+            }
+          }
+        continue;
+      }
+    }
+    tuple_exact<Real, KM>(w, a, sg, bp, ctrl);
+  }
+  __syncthreads();
+  // ---- Compress(S) ----
+  for (int g = 0; g < a.G; ++g) {
+    if (any_pt && w.m->pt[g] >= 0) w.pass_through(blks[w.m->pt[g]], blks[g], a);
+    else w.encode(g, blks[g], a);
+  }
+}
+
+template <typename Real, int KM>
+__device__ __forceinline__ void pass_body(const PassArgs& a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const Layout L = make_layout(a.b, a.G, (int)sizeof(Real));
+  Worker<Real> w;
+  w.init(smem, L, a.b, a.qp);
+  // A state poisoned by an earlier pass (or by another CTA of this one) is skipped. One
+  // thread reads the flag so that the whole CTA takes the same branch.
+  if (threadIdx.x == 0) {
+    w.m->err = 0;
+    w.m->live = *(volatile unsigned int*)&a.sc->status == 0;
+  }
+  __syncthreads();
+  if (w.m->live) {
+    const double sigma = a.use_sigma ? *(volatile double*)&a.sc->sigma : 1.0;
+    FastGate* fg = (FastGate*)(smem + L.off_fast);
+    if (sizeof(Real) == 8 && threadIdx.x == 0) fast_prepare(fg, a, sigma);  // visible after pass_group's barrier
+    for (unsigned long long grp = blockIdx.x; grp < a.ngroups; grp += gridDim.x)
+      pass_group<Real, KM>(w, a, fg, sigma, grp);
+    if (threadIdx.x == 0 && w.m->err) {
+      atomicOr(&a.sc->status, w.m->err);
+      atomicMin(&a.sc->fail_seq, a.seq);
+    }
+  }
+}
+
+// The pass kernel without a register cap, and (COMPACT) with one: 64 registers per thread,
+// spilling, so that four 256-thread CTAs fit on an SM.
+template <typename Real, int KM>
+__global__ void __launch_bounds__(256) k_pass(const PassArgs a) {
+  pass_body<Real, KM>(a);
+}
+template <typename Real, int KM>
+__global__ void __launch_bounds__(256, 4) k_pass_c(const PassArgs a) {
+  pass_body<Real, KM>(a);
+}
+
+
+template <typename Real, int KM, bool COMPACT>
+static cudaError_t launch_pass_k(const PassArgs& a, cudaStream_t st) {
+  const Layout L = make_layout(a.b, a.G, (int)sizeof(Real));
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e;
+    if constexpr (COMPACT) e = cudaFuncSetAttribute(k_pass_c<Real, KM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    else e = cudaFuncSetAttribute(k_pass<Real, KM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  if (L.total > 227 * 1024) return cudaErrorInvalidValue;
+  const int T = threads_ok(a.b, a.threads) ? a.threads : worker_threads(a.b);
+  unsigned long long grid = a.ngroups;
+  if (grid > 0x7fffffffull) grid = 0x7fffffffull;
+  if constexpr (COMPACT) k_pass_c<Real, KM><<<(unsigned int)grid, T, L.total, st>>>(a);
+  else k_pass<Real, KM><<<(unsigned int)grid, T, L.total, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename Real>
+static cudaError_t launch_pass_t(const PassArgs& a, cudaStream_t st) {
+  if (a.K <= 2) return launch_pass_k<Real, 2, false>(a, st);
+  if (a.K <= 4) return launch_pass_k<Real, 4, false>(a, st);
+  return launch_pass_k<Real, 8, false>(a, st);
+}
+
+}  // namespace sv

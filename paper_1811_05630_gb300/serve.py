@@ -53,8 +53,9 @@ def size_class(n: int) -> int:
 
 class Server:
     def __init__(self, pool_bytes: int, budget_bytes: int, block_log2: int = 10, max_batch: int = 64,
-                 graphs: bool = True, keep_results: bool = False):
+                 graphs: bool = True, keep_results: bool = False, threads: int = 128):
         self.pool = sv.Pool(pool_bytes)
+        self.threads = threads  # CTA size of the fused pass where the block size allows it
         self.budget = budget_bytes
         self.block_log2 = block_log2
         self.max_batch = max_batch
@@ -100,6 +101,9 @@ class Server:
                 self._bucket(key)
                 st = sv.State(self.pool, req.n, req.n, req.eb, req.dtype, block_log2=key[1],
                               stream=self.streams[key])
+                nv = 2 << key[1]
+                if 32 <= self.threads <= 256 and 2 <= nv // self.threads <= 32:
+                    st.set_threads(self.threads)
                 st.reset_basis(req.basis)
                 used += fp
                 active[key].append([req, st, 0, now, fp])

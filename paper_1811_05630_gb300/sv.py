@@ -70,6 +70,7 @@ _SIGS = {
     "sv_apply_gate": ([_vp, _vp, _vp, _i, _vp, _i], _i),
     "sv_sync": ([_vp], _i),
     "sv_set_threads": ([_vp, _i], _i),
+    "sv_set_compact": ([_vp, _i], _i),
     "sv_measure_probs": ([_vp, _vp, _i, _vp], _i),
     "sv_amplitudes": ([_vp, _vp, _sz, _vp], _i),
     "sv_read_amplitudes": ([_vp, _u64, _u64, _vp], _i),
@@ -175,6 +176,10 @@ class State:
     def set_threads(self, threads: int) -> None:
         """CTA size of the fused pass (0: default); results do not depend on it."""
         _check(_L.sv_set_threads(self._h, int(threads)), "sv_set_threads")
+
+    def set_compact(self, on: bool) -> None:
+        """Register-capped build of the fused pass for 1- and 2-qubit gates (results unchanged)."""
+        _check(_L.sv_set_compact(self._h, 1 if on else 0), "sv_set_compact")
 
     def stats(self) -> dict:
         st = Stats()

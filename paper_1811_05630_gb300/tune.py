@@ -1,11 +1,13 @@
-"""Autotuner for the block size (block_log2) and the CTA size of the fused pass.
+"""Autotuner for the block size (block_log2), the CTA size and the register budget of the
+fused pass.
 
 The block size sets the codec's parallel unit: small blocks give more CTAs per pass and
 more CTAs per SM (less shared memory each), large blocks amortize the per-block codebook
 and headers. The CTA size (threads per block-group) trades per-block latency against CTAs
-resident per SM (registers). The best pair depends on the state size, dtype, error bound and
+resident per SM; the register-capped build (64 registers per thread, spilling) fits four
+256-thread CTAs on an SM. The best pair depends on the state size, dtype, error bound and
 circuit, so the tuner times a few gate passes of a representative circuit for each candidate
-on the GPU (fused-kernel CUDA events) and keeps the fastest. Neither knob changes results.
+on the GPU (fused-kernel CUDA events) and keeps the fastest. No knob changes results.
 Results are cached in a JSON file keyed by (GPU name, dtype, qubits, error bound, circuit
 kind).
 """
@@ -53,12 +55,13 @@ def thread_candidates(b: int) -> List[int]:
 
 
 def probe(pool: sv.Pool, n: int, dtype: int, eb: float, b: int, prefix: Sequence[Gate], timed: Sequence[Gate],
-          basis: int = 0, threads: int = 0) -> float:
-    """Fused-kernel milliseconds per pass for `timed` after `prefix`, at block size b and CTA
-    size `threads` (0: the default)."""
+          basis: int = 0, threads: int = 0, compact: bool = False) -> float:
+    """Fused-kernel milliseconds per pass for `timed` after `prefix`, at block size b, CTA
+    size `threads` (0: the default) and with or without the register-capped build."""
     st = sv.State(pool, n, n, eb, dtype, block_log2=b)
     try:
         st.set_threads(threads)
+        st.set_compact(compact)
         st.reset_basis(basis)
         st.run(prefix)
         st.sync()
@@ -73,11 +76,11 @@ def probe(pool: sv.Pool, n: int, dtype: int, eb: float, b: int, prefix: Sequence
 def best_config(n: int, dtype: int, eb: float, kind: str, prefix: Sequence[Gate], timed: Sequence[Gate],
                 basis: int = 0, candidates: Iterable[int] = (8, 9, 10, 11, 12), pool: Optional[sv.Pool] = None,
                 use_cache: bool = True) -> dict:
-    """Tune (block_log2, threads) for a workload; returns {"block_log2": b, "threads": T,
-    "ms_per_pass": {"b/T": ms}}."""
+    """Tune (block_log2, threads, register-capped build) for a workload; returns
+    {"block_log2": b, "threads": T, "compact": c, "ms_per_pass": {"b/T/c": ms}}."""
     key = _key(n, dtype, eb, kind)
     cache = _load() if use_cache else {}
-    if key in cache and "threads" in cache[key]:
+    if key in cache and "compact" in cache[key]:
         return cache[key]
     own = pool is None
     if own:
@@ -88,13 +91,14 @@ def best_config(n: int, dtype: int, eb: float, kind: str, prefix: Sequence[Gate]
             if b > n:
                 continue
             for t in thread_candidates(b):
-                times[(b, t)] = probe(pool, n, dtype, eb, b, prefix, timed, basis, threads=t)
+                for c in ((0, 1) if t >= 128 else (0,)):
+                    times[(b, t, c)] = probe(pool, n, dtype, eb, b, prefix, timed, basis, threads=t, compact=bool(c))
     finally:
         if own:
             pool.close()
     best = min(times, key=times.get)
-    res = {"block_log2": best[0], "threads": best[1],
-           "ms_per_pass": {"%d/%d" % k: v for k, v in sorted(times.items())}}
+    res = {"block_log2": best[0], "threads": best[1], "compact": bool(best[2]),
+           "ms_per_pass": {"%d/%d/%d" % k: v for k, v in sorted(times.items())}}
     if use_cache:
         cache[key] = res
         _store(cache)

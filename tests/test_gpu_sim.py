@@ -153,13 +153,14 @@ def _gate(m, targets, controls=(), name=""):
     return C.Gate(np.asarray(m, dtype=np.complex128), tuple(targets), tuple(controls), name)
 
 
-def run_compare_reuse(sv, pool, n, b, dtype, eb, x, gates, threads=0):
+def run_compare_reuse(sv, pool, n, b, dtype, eb, x, gates, threads=0, compact=False):
     """run_compare, gate by gate, summing the blocks each pass re-emitted unchanged."""
     st = sv.State(pool, n, n, eb, dtype, block_log2=b)
     reused = 0
     try:
         if threads:
             st.set_threads(threads)
+        st.set_compact(compact)
         st.reset_basis(x)
         cs = oracle.CompressedSim(n, n, b, dtype, eb, x)
         for i, g in enumerate(gates):
@@ -195,6 +196,15 @@ def test_stream_pass_through_bit_exact(sv, pool):
     assert reused > 0
 
 
+@pytest.mark.parametrize("dtype", [oracle.C128, oracle.C64])
+def test_zero_blocks_pass_through_bit_exact(sv, pool, dtype):
+    # QFT of a basis state: the early stages leave most blocks all zero, which every gate
+    # maps to zero; both precisions re-emit them and still match the oracle
+    n, b = 12, 5
+    reused = run_compare_reuse(sv, pool, n, b, dtype, 1e-6, C.seeded_index(7, n), C.qft(n)[:30])
+    assert reused > 0
+
+
 def test_pass_through_rejects_verbatim_and_rescaled_blocks(sv, pool):
     # Grover at eb 4e-10 stores the large marked amplitude verbatim (|x| > 2^29 * 2eb), and
     # a non-unitary gate moves sigma far from 1: blocks with a verbatim value or a code
@@ -208,11 +218,14 @@ def test_pass_through_rejects_verbatim_and_rescaled_blocks(sv, pool):
     assert reused > 0
 
 
-@pytest.mark.parametrize("threads", [64, 128, 256])
-def test_cta_size_does_not_change_results(sv, pool, threads):
-    n, b = 12, 10  # default CTA size 64; 128 and 256 idle part of the CTA while decoding
+@pytest.mark.parametrize("threads,compact", [(64, False), (128, False), (256, False), (256, True), (128, True)])
+@pytest.mark.parametrize("dtype", [oracle.C128, oracle.C64])
+def test_launch_shape_does_not_change_results(sv, pool, threads, compact, dtype):
+    # default CTA size 64 at block_log2 10; 128 and 256 idle part of the CTA while decoding;
+    # the register-capped build spills but must compute the same bytes
+    n, b = 12, 10
     gates = C.qft(n)[:20] + C.random_brickwork(n, 1, seed=8)
-    run_compare_reuse(sv, pool, n, b, oracle.C128, 1e-7, C.seeded_index(6, n), gates, threads=threads)
+    run_compare_reuse(sv, pool, n, b, dtype, 1e-7, C.seeded_index(6, n), gates, threads=threads, compact=compact)
 
 
 def test_cta_size_checked(sv, pool):
@@ -246,6 +259,14 @@ def test_plain_path_matches_o1(sv, pool, dtype, tol):
     for _ in range(6):
         qs = [int(q) for q in rng.permutation(n)]
         gates.append(C.Gate(random_unitary(rng, 8), tuple(qs[:3]), (qs[3],), "U3"))
+    # the plain kernel's diagonal and permutation forms, with and without controls
+    gates += C.grover(n, 1234, 1)
+    P3 = np.eye(8, dtype=np.complex128)[[3, 0, 6, 1, 2, 7, 4, 5]]
+    D3 = np.diag(np.exp(1j * rng.uniform(0, 2 * np.pi, 8)))
+    D3[0, 0] = D3[5, 5] = 1.0
+    gates += [C.Gate(P3, (2, 9, 5), (0,), "P3"), C.Gate(P3, (11, 1, 4), (), "P3"),
+              C.Gate(D3, (3, 10, 6), (7, 8), "D3"), C.Gate(np.eye(2, dtype=np.complex128), (4,), (), "I"),
+              C.Gate(-np.eye(4, dtype=np.complex128), (0, 1), (2,), "-I")]
     st = sv.State(pool, n, n, 0.0, dtype)
     try:
         st.run(gates)
