@@ -417,6 +417,10 @@ def run_full_circuit(args):
     wl = workload(args.workload)
     if args.block_log2:
         wl["block_log2"] = args.block_log2
+    if args.eb:
+        wl["eb"] = args.eb
+    if args.dtype:
+        wl["dtype"] = {"c128": 2, "c64": 1}[args.dtype]
     n, gates = wl["n"], wl["gates"]
     pool = sv.Pool(int(args.pool_gb * (1 << 30)))
     st = sv.State(pool, n, wl["slice_log2"], wl["eb"], wl["dtype"], block_log2=wl["block_log2"],
@@ -435,8 +439,13 @@ def run_full_circuit(args):
     st.set_pass_timing(True)
     with ClockSampler(0) as clk:
         for i, g in enumerate(gates):
-            st.apply(g.matrix, g.targets, g.controls)
-            stt = st.stats()  # synchronizes: per-gate compressed size
+            try:
+                st.apply(g.matrix, g.targets, g.controls)
+                stt = st.stats()  # synchronizes: per-gate compressed size
+            except sv.SvError as ex:
+                # e.g. every amplitude quantized to zero (a bound far above the amplitudes)
+                return {"workload": wl["desc"], "dtype": wl["dtype"], "eb": wl["eb"], "gates_done": i,
+                        "error": str(ex), "bytes_per_gate": per_gate}
             per_gate.append(stt["compressed_bytes"])
             reused += stt["blocks_reused"]
     wall = time.time() - t_all
@@ -452,7 +461,8 @@ def run_full_circuit(args):
     norm = st.norm()
     samp = np.abs(amps) ** 2 / norm * (1 << n)
     res = {
-        "workload": wl["desc"], "block_log2": wl["block_log2"], "threads_per_cta": args.threads or "default",
+        "workload": wl["desc"], "dtype": wl["dtype"], "eb": wl["eb"],
+        "block_log2": wl["block_log2"], "threads_per_cta": args.threads or "default",
         "register_capped_build": args.compact,
         "gates": len(gates), "blocks_reused_fraction": reused / (len(gates) * stt["n_blocks"]),
         "replayed_passes": stt["replayed_passes"],
@@ -467,6 +477,28 @@ def run_full_circuit(args):
         "pool_used_bytes": pool_used, "clocks": clk.summary(),
         "bytes_per_gate": per_gate,
     }
+    if fid is None and args.plain:
+        # no closed form: the plain GPU path runs the whole circuit beside the compressed
+        # state and the fidelity is taken between the two final states
+        try:
+            ppool = sv.Pool(raw + (256 << 20))
+            ps = sv.State(ppool, n, n, 0.0, wl["dtype"])
+            ps.reset_basis(x)
+            ps.sync()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ps.run(gates)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            res["plain_amp_updates_per_s_whole_circuit"] = (1 << n) * len(gates) / (e0.elapsed_time(e1) * 1e-3)
+            res["fidelity_vs_plain"] = st.fidelity(ps)
+            ps.close()
+            ppool.close()
+        except Exception as ex:  # noqa: BLE001
+            res["plain_amp_updates_per_s_whole_circuit"] = "unavailable: %s" % ex
+        st.close()
+        pool.close()
+        return res
     st.close()
     pool.close()
     del st, pool
@@ -539,6 +571,8 @@ def main():
     ap.add_argument("--block-log2", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0, help="CTA size of the fused pass (0: tuned/default)")
     ap.add_argument("--compact", action="store_true", help="register-capped build of the fused pass")
+    ap.add_argument("--eb", type=float, default=0.0, help="override the workload's error bound (full-circuit mode)")
+    ap.add_argument("--dtype", choices=["c128", "c64"], default=None, help="override the workload's dtype (full-circuit mode)")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="use the workload's fixed block size instead of tuning it")
     ap.add_argument("--pool-gb", type=float, default=8.0)

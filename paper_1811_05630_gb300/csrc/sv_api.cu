@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -131,11 +132,11 @@ struct sv_state {
   unsigned long long replayed = 0;  // passes re-run after an arena overflow
   int threads = 0;                  // CTA size of the fused pass (0: default)
   bool compact = false;             // register-capped build of the pass (1- and 2-qubit gates)
-  // passes between status checks: every pass while the state grows, 8 after an overflow,
-  // doubling per clean check up to 256 (an overflow poisons every later pass until the
-  // check replays them)
+  // passes between status checks (an overflow poisons every later pass until the check
+  // replays them): about 2 ms of device work, 1 after an overflow
   int sync_every = 16;
-  size_t last_live = 0;  // stream bytes of the state at the last clean check
+  std::chrono::steady_clock::time_point last_check = std::chrono::steady_clock::now();
+  unsigned long long since_check = 0;  // passes submitted since the last clean check
 };
 
 namespace {
@@ -329,6 +330,7 @@ int log_step(sv_state* s, Logged&& lg) {
   s->cur ^= 1;
   if (s->sticky_err) return SV_OK;
   s->log.push_back(std::move(lg));
+  s->since_check++;
   if (s->log.size() >= (size_t)s->sync_every) {
     const int rc = sv_sync(s);
     if (rc == SV_ERR_CUDA) return rc;
@@ -600,12 +602,19 @@ int sv_sync(sv_state* s) {
     if (rc) return rc;
     if (h.status == 0) {
       s->log.clear();
-      // check often while the state grows (an overflow costs a replay of every pass since
-      // the failed one), rarely once it does not
+      // an overflow costs a replay of every pass since the failed one: check about every
+      // 2 ms of device work (the passes since the last check, over the time they took), at
+      // most 256 passes apart
+      const auto now = std::chrono::steady_clock::now();
+      if (s->since_check > 0) {
+        const double per_pass =
+            std::chrono::duration<double>(now - s->last_check).count() / (double)s->since_check;
+        const double n = per_pass > 0.0 ? 2e-3 / per_pass : 256.0;
+        s->sync_every = n >= 256.0 ? 256 : (n <= 1.0 ? 1 : (int)n);
+      }
+      s->last_check = now;
+      s->since_check = 0;
       const size_t live = (size_t)h.bump[s->cur];
-      const bool growing = live > s->last_live + s->last_live / 8;
-      s->sync_every = growing ? 1 : std::min(256, s->sync_every * 2);
-      s->last_live = live;
       // the arena the next pass writes gets room for twice the current state
       rc = reserve_arena(s, s->cur ^ 1, 2 * live);
       if (rc) return rc;
@@ -623,7 +632,7 @@ int sv_sync(sv_state* s) {
     for (auto& ev : s->ev_pending) s->ev_free.push_back(ev);
     s->ev_pending.clear();
     if (h.status != kStOverflow) return status_to_err(h.status);
-    s->sync_every = 8;
+    s->sync_every = 1;
     // find the failed pass in the log
     size_t i = 0;
     while (i < s->log.size() && s->log[i].seq != h.fail_seq) ++i;

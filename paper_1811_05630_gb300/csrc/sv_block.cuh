@@ -332,6 +332,7 @@ struct Worker {
         if (tid < C) cstart[tid] = cs;
         if (tid == 0) cstart[C] = pbits;
         // decode table: every code of length <= kLutBits fills its 2^(kLutBits-l) entries
+        // with (symbol << 8) | length (never 0: length >= 1)
         for (int i = tid; i < D; i += T) {
           int l = 1;
           while (l < lmax && !(i >= m->offs[l] && i < m->offs[l] + m->lcount[l])) ++l;
@@ -339,7 +340,7 @@ struct Worker {
           if (l <= kLutBits) {
             const uint32_t lo = code << (kLutBits - l), n = 1u << (kLutBits - l);
             if (lo + n <= (1u << kLutBits))
-              for (uint32_t e = 0; e < n; ++e) lut[lo + e] = ((uint32_t)(i + 1) << 8) | (uint32_t)l;
+              for (uint32_t e = 0; e < n; ++e) lut[lo + e] = ((uint32_t)symtab[i] << 8) | (uint32_t)l;
           }
         }
       }
@@ -428,11 +429,12 @@ struct Worker {
       }
       const uint32_t pk = (uint32_t)(buf >> 32);
       const uint32_t e = lut[pk >> (32 - kLutBits)];
-      int idx = -1, l = 0;
-      if (e) {
-        idx = (int)(e >> 8) - 1;
+      int sym, l;
+      if (e) {  // short code: symbol and length straight from the table
+        sym = (int)(e >> 8);
         l = (int)(e & 0xff);
       } else {
+        int idx = -1;
         for (l = kLutBits + 1; l <= lmax; ++l) {
           const int c = (int)(pk >> (32 - l));
           if (m->lcount[l] && c >= m->first[l] && c - m->first[l] < m->lcount[l]) {
@@ -440,15 +442,15 @@ struct Worker {
             break;
           }
         }
-      }
-      if (idx < 0 || idx >= D) {
-        cerr = true;
-        break;
+        if (idx < 0 || idx >= D) {
+          cerr = true;
+          break;
+        }
+        sym = symtab[idx];
       }
       buf <<= l;
       nbuf -= l;
       pos += (uint32_t)l;
-      const int sym = symtab[idx];
       int32_t d;
       if (sym == 0) {
         if (nbuf < 32) {
@@ -712,20 +714,24 @@ __device__ inline void huffman_merge(const uint32_t* keys, int D, uint32_t* wint
 }
 
 // Depth of every node of the merged tree by pointer jumping (all threads): d[v] += d[p[v]],
-// p[v] = p[p[v]], ping-ponging between two copies. Depths are at most 18 for the <= 8192
-// symbols of a block, so 6 rounds (jumps of 64) reach the root from every node and leave the
-// result in (parent, depth).
-__device__ inline void tree_depths(int D, uint16_t* parent, uint8_t* depth, uint16_t* parent2,
-                                   uint8_t* depth2) {
+// p[v] = p[p[v]], ping-ponging between two copies. A tree over D leaves is at most D - 1
+// deep, and a Huffman tree over the <= 8192 symbols of a block at most 18 (a code of length L
+// needs total weight >= Fibonacci(L + 2)); after k rounds every node has jumped 2^k levels, so
+// the first k with 2^k >= min(D - 1, 18) suffices. Returns the array holding the depths.
+__device__ inline uint8_t* tree_depths(int D, uint16_t* parent, uint8_t* depth, uint16_t* parent2,
+                                       uint8_t* depth2) {
   const int total = 2 * D - 1, root = total - 1;
   for (int v = threadIdx.x; v < total; v += blockDim.x) {
     depth[v] = v == root ? 0 : 1;
     if (v == root) parent[v] = (uint16_t)root;
   }
   __syncthreads();
+  const int maxd = D - 1 < 18 ? D - 1 : 18;
+  int rounds = 0;
+  while ((1 << rounds) < maxd) ++rounds;
   uint16_t *pa = parent, *pb = parent2;
   uint8_t *da = depth, *db = depth2;
-  for (int round = 0; round < 6; ++round) {
+  for (int round = 0; round < rounds; ++round) {
     for (int v = threadIdx.x; v < total; v += blockDim.x) {
       const int p = pa[v];
       db[v] = (uint8_t)(da[v] + da[p]);
@@ -739,6 +745,7 @@ __device__ inline void tree_depths(int D, uint16_t* parent, uint8_t* depth, uint
     da = db;
     db = td;
   }
+  return da;
 }
 
 // Sort n (key, val) pairs ascending by key (keys distinct). Up to 256: every element finds
@@ -893,7 +900,7 @@ __device__ void Worker<Real>::encode(int g, unsigned long long blk, const PassAr
       } else {
         if (tid == 0) huffman_merge(keys, D, wint, parent);
         __syncthreads();
-        tree_depths(D, parent, lens, parent2, lens2);
+        lens = tree_depths(D, parent, lens, parent2, lens2);
       }
       if (tid == 0) m->lmax = 0;
       __syncthreads();
