@@ -92,8 +92,10 @@ int sv_pool_usage(const sv_pool* pool, size_t* used_bytes, size_t* capacity_byte
  *   dtype      SV_C64 or SV_C128.
  *   stream     cudaStream_t (as void*) all work of this state is ordered on.
  * Block size: min(slice_log2, 12) unless sv_create_ex sets it (5..12; -1 = default).
- * arena_bytes (sv_create_ex): initial capacity of each of the two arenas (0 = default,
- *   64 bytes per block, at least one 2 MiB page); arenas grow on overflow (sv_sync).
+ * arena_bytes (sv_create_ex): capacity of each of the two arenas (0 = default: 64 bytes
+ *   per block, at least one 2 MiB page, and at every status check the arena the next pass
+ *   writes is reserved at twice the live state); arenas grow on overflow (sv_sync), and a
+ *   caller-given size grows on overflow only.
  * Returns SV_ERR_OOM when the pool cannot hold the state's initial arenas.
  * ------------------------------------------------------------------------------------- */
 int sv_create(sv_pool* pool, int n_qubits, int slice_log2, double error_bound, int dtype,

@@ -135,6 +135,7 @@ struct sv_state {
   // passes between status checks (an overflow poisons every later pass until the check
   // replays them): about 2 ms of device work, 1 after an overflow
   int sync_every = 16;
+  bool fixed_arena = false;  // the caller sized the arenas: they grow on overflow only
   std::chrono::steady_clock::time_point last_check = std::chrono::steady_clock::now();
   unsigned long long since_check = 0;  // passes submitted since the last clean check
 };
@@ -517,6 +518,7 @@ int sv_create_ex(sv_pool* pool, int n, int sl, int bl, double eb, int dtype, siz
   s->tree = (double*)(m + o_tree);
   // arenas: the initial state is nearly all 16-byte CONST blocks
   const size_t init_cap = arena_bytes ? arena_bytes : std::max<size_t>(kPage, nb * 64);
+  s->fixed_arena = arena_bytes != 0;
   for (int id = 0; id < 2; ++id) {
     if (!region_alloc(pool, &s->arena_r[id], init_cap)) {
       region_free(pool, &s->arena_r[0]);
@@ -616,8 +618,10 @@ int sv_sync(sv_state* s) {
       s->since_check = 0;
       const size_t live = (size_t)h.bump[s->cur];
       // the arena the next pass writes gets room for twice the current state
-      rc = reserve_arena(s, s->cur ^ 1, 2 * live);
-      if (rc) return rc;
+      if (!s->fixed_arena) {
+        rc = reserve_arena(s, s->cur ^ 1, 2 * live);
+        if (rc) return rc;
+      }
       for (auto& ev : s->ev_pending) {
         float ms = 0.f;
         cudaEventElapsedTime(&ms, ev.first, ev.second);

@@ -28,6 +28,16 @@ struct Misc {
   uint32_t size;
   unsigned long long out_off;
   int ok;
+  // complex128 blocks with more verbatim values than the lists hold: inputs are read from
+  // the stream by rank; outputs are found again by a second transform (fix) that writes
+  // their raw values straight into the already written output stream
+  int vin_big[4];
+  const uint64_t* vin_vals[4];
+  int vbig[4];
+  int any_big;
+  int fix;
+  uint8_t* vsec_base[4];
+  uint32_t vsec_valoff[4];
   int pt[4];       // pass-through source slot per block of the group (-1: recode)
   unsigned int dmask;  // blocks of the group to decode
   int npt;
@@ -108,7 +118,8 @@ struct FastGate {
 struct Layout {
   int nv, G, hs, dcap, p2cap;
   uint32_t off_q, off_vin_pos, off_vin_bits, off_vout_pos, off_vout_bits, off_hkey, off_hval,
-      off_stage, off_build, off_misc, off_fast, off_desc, off_vmask, off_vtree, total;
+      off_stage, off_build, off_misc, off_fast, off_desc, off_vmask, off_vtree, off_vomask, off_vpre_in,
+      off_vpre_out, total;
   uint32_t stage_bytes, build_bytes;
   uint32_t sort_off, sort_n;  // rank-sort scratch inside the build area
   uint32_t off_wint, off_parent, off_parent2, off_lens, off_lens2;
@@ -172,6 +183,14 @@ __host__ __device__ inline Layout make_layout(int b, int G, int csize) {
   o += (uint32_t)pad_to((size_t)G * (L.nv / 32) * 4, 16);
   L.off_vtree = o;  // pairwise verbatim-square tree across threads
   o += 256 * 8;
+  // complex128: output verbatim bitmap, and per-word prefix counts of the input and output
+  // bitmaps (ranks of verbatim values in their stream sections)
+  L.off_vomask = o;
+  o += (uint32_t)pad_to((size_t)G * (L.nv / 32) * 4, 16);
+  L.off_vpre_in = o;
+  o += (uint32_t)pad_to((size_t)G * (L.nv / 32) * 2, 16);
+  L.off_vpre_out = o;
+  o += (uint32_t)pad_to((size_t)G * (L.nv / 32) * 2, 16);
   L.total = o;
   return L;
 }
@@ -208,6 +227,8 @@ struct Worker {
   static constexpr bool kMask = sizeof(Real) == 4;
   uint32_t* vmask;
   double* vtree;
+  uint32_t* vomask;
+  uint16_t *vpre_in, *vpre_out;
 
   __device__ void init(unsigned char* smem, const Layout& lay, int b_, const QuantP& p) {
     L = lay;
@@ -227,6 +248,9 @@ struct Worker {
     m = (Misc*)(smem + L.off_misc);
     vmask = (uint32_t*)(smem + L.off_vmask);
     vtree = (double*)(smem + L.off_vtree);
+    vomask = (uint32_t*)(smem + L.off_vomask);
+    vpre_in = (uint16_t*)(smem + L.off_vpre_in);
+    vpre_out = (uint16_t*)(smem + L.off_vpre_out);
     vin_cnt = m->vin_cnt;
     vout_cnt = m->vout_cnt;
   }
@@ -239,8 +263,8 @@ struct Worker {
   __device__ void decode(int g, const uint8_t* s, uint32_t len) {
     const int tid = threadIdx.x, nv = L.nv;
     int32_t* qb = q + g * nv;
-    if (kMask)
-      for (int i = tid; i < (nv >> 5); i += T) vmask[g * (nv >> 5) + i] = 0u;
+    for (int i = tid; i < (nv >> 5); i += T) vmask[g * (nv >> 5) + i] = 0u;
+    if (tid == 0) m->vin_big[g] = 0;
     // header and body are staged (they always fit); a complex64 verbatim section can be
     // longer than the stage and is read from the stream in global memory
     const bool fits = len >= kHdr && (len & 15) == 0;
@@ -350,34 +374,41 @@ struct Worker {
     }
     if (bad && tid == 0) atomicOr(&m->err, kStCorrupt);
     __syncthreads();
-    // inverse Lorenzo: q_j = q_{j-2} + delta_j, one running sum per plane
+    // inverse Lorenzo: q_j = q_{j-2} + delta_j, one running sum per plane (each thread sums
+    // its run, a block scan gives the run's offsets, then a second sweep writes the codes;
+    // the deltas are read twice from shared memory rather than held in registers)
     int2 loc = make_int2(0, 0);
-    int32_t dv[32];
-#pragma unroll
-    for (int i = 0; i < 32; ++i)
-      if (i < vpt) {
-        dv[i] = qb[tid * vpt + i];
-        if (i & 1) loc.y += dv[i];
-        else loc.x += dv[i];
-      }
+    int32_t* run = qb + tid * vpt;
+    for (int i = 0; i < vpt; i += 2) {
+      loc.x += run[i];
+      loc.y += run[i + 1];
+    }
     int2 off = block_excl_scan_i2(loc, (int2*)m->red);
-#pragma unroll
-    for (int i = 0; i < 32; ++i)
-      if (i < vpt) {
-        if (i & 1) {
-          off.y += dv[i];
-          qb[tid * vpt + i] = off.y;
-        } else {
-          off.x += dv[i];
-          qb[tid * vpt + i] = off.x;
-        }
-      }
+    for (int i = 0; i < vpt; i += 2) {
+      off.x += run[i];
+      off.y += run[i + 1];
+      run[i] = off.x;
+      run[i + 1] = off.y;
+    }
     // verbatim section: ascending positions, then raw values (aligned to the value size)
-    if (nverb > (kMask ? nv : kVmax)) {
-      if (tid == 0) atomicOr(&m->err, kStVerbatim);
+    if (nverb > nv) {
+      if (tid == 0) atomicOr(&m->err, kStCorrupt);
     } else if (nverb > 0 && !bad) {
       __syncthreads();
       read_verbatim(g, s, body_end, total, nverb);
+      if (!kMask && nverb > kVmax) {
+        // rank of a verbatim value = verbatim positions before it: per-word prefix counts
+        __syncthreads();
+        const int W = nv >> 5;  // <= blockDim.x (threads_ok)
+        const uint32_t pc = tid < W ? (uint32_t)__popc(vmask[g * W + tid]) : 0u;
+        uint32_t tot = 0;
+        const uint32_t pre = block_excl_scan_u32(pc, m->scan, &tot);
+        if (tid < W) vpre_in[g * W + tid] = (uint16_t)pre;
+        if (tid == 0) {
+          m->vin_big[g] = 1;
+          m->vin_vals[g] = (const uint64_t*)(s + pad_to(body_end + 2 * nverb, 8));
+        }
+      }
     }
     if (tid == 0) vin_cnt[g] = (!kMask && nverb <= kVmax) ? nverb : 0;
     __syncthreads();
@@ -399,6 +430,9 @@ struct Worker {
         atomicOr(&m->err, kStCorrupt);
       } else if (kMask) {
         q[g * L.nv + j] = (int32_t)(uint32_t)bits;
+        atomicOr(&vmask[g * (L.nv >> 5) + (j >> 5)], 1u << (j & 31));
+      } else if (nverb > kVmax) {  // looked up by rank in the stream (value_at)
+        q[g * L.nv + j] = kSentinel;
         atomicOr(&vmask[g * (L.nv >> 5) + (j >> 5)], 1u << (j & 31));
       } else {
         vin_pos[g * kVmax + i] = (uint16_t)j;
@@ -475,8 +509,8 @@ struct Worker {
     const int tid = threadIdx.x;
     int32_t* qb = q + g * L.nv;
     for (int j = tid; j < L.nv; j += T) qb[j] = 0;
-    if (kMask)
-      for (int i = tid; i < (L.nv >> 5); i += T) vmask[g * (L.nv >> 5) + i] = 0u;
+    for (int i = tid; i < (L.nv >> 5); i += T) vmask[g * (L.nv >> 5) + i] = 0u;
+    if (tid == 0) m->vin_big[g] = 0;
     __syncthreads();
     if (kMask) {
       if (tid == 0) {
@@ -515,6 +549,12 @@ struct Worker {
     const int32_t c = q[g * L.nv + j];
     if (kMask) return is_verb(g, j) ? RawBits<Real>::from((uint32_t)c) : dequant<Real>(c, qp);
     if (c != kSentinel) return dequant<Real>(c, qp);
+    if (m->vin_big[g]) {
+      const int W = L.nv >> 5;
+      const uint32_t wd = vmask[g * W + (j >> 5)];
+      const uint32_t rank = vpre_in[g * W + (j >> 5)] + (uint32_t)__popc(wd & ((1u << (j & 31)) - 1u));
+      return RawBits<Real>::from(__ldg(m->vin_vals[g] + rank));
+    }
     const int n = vin_cnt[g];
     for (int i = 0; i < n; ++i)
       if (vin_pos[g * kVmax + i] == j) return RawBits<Real>::from(vin_bits[g * kVmax + i]);
@@ -549,14 +589,23 @@ struct Worker {
       }
       return;
     }
-    if (quantize<Real>(v, qp, &c)) {
+    const bool verb = quantize<Real>(v, qp, &c);
+    if (m->fix) {  // second transform of a block with many verbatim values: raw values only
+      if (verb && m->vbig[g]) {
+        const int W = L.nv >> 5;
+        const uint32_t wd = vomask[g * W + (j >> 5)];
+        const uint32_t rank = vpre_out[g * W + (j >> 5)] + (uint32_t)__popc(wd & ((1u << (j & 31)) - 1u));
+        *(uint64_t*)(m->vsec_base[g] + m->vsec_valoff[g] + 8 * rank) = RawBits<Real>::to(v);
+      }
+      return;
+    }
+    if (verb) {
       const int i = atomicAdd(&vout_cnt[g], 1);
       if (i < kVmax) {
         vout_pos[g * kVmax + i] = (uint16_t)j;
         vout_bits[g * kVmax + i] = RawBits<Real>::to(v);
-      } else {
-        atomicOr(&m->err, kStVerbatim);
       }
+      atomicOr(&vomask[g * (L.nv >> 5) + (j >> 5)], 1u << (j & 31));
       c = 0;
     }
     q[g * L.nv + j] = c;
@@ -609,18 +658,28 @@ struct Worker {
 
   // complex64: write the verbatim section (u16 positions ascending, raw floats) of block g
   // into its stream at `out`, after the zero fill of the section
+  // (complex128 with many verbatim values: positions now; per-word prefix counts and the
+  // section's address kept for the second transform that writes the raw values)
   __device__ void write_verbatim_inplace(int g, uint8_t* out, uint32_t body_end, int nverb) {
     const int tid = threadIdx.x, nv = L.nv, j0 = tid * vpt;
-    const uint32_t w = vmask[g * (nv >> 5) + (j0 >> 5)];
+    const uint32_t* bm = kMask ? vmask : vomask;
+    const uint32_t w = bm[g * (nv >> 5) + (j0 >> 5)];
     const uint32_t mine = vpt >= 32 ? w : ((w >> (j0 & 31)) & ((1u << vpt) - 1u));
     uint32_t tot = 0;
     uint32_t k = block_excl_scan_u32((uint32_t)__popc(mine), m->scan, &tot);
     const uint32_t valoff = (uint32_t)pad_to(body_end + 2 * nverb, sizeof(Real));
+    if (!kMask) {
+      if ((j0 & 31) == 0) vpre_out[g * (nv >> 5) + (j0 >> 5)] = (uint16_t)k;  // vpt <= 32: word start
+      if (tid == 0) {
+        m->vsec_base[g] = out;
+        m->vsec_valoff[g] = valoff;
+      }
+    }
     for (int i = 0; i < vpt; ++i) {
       if (!((mine >> i) & 1u)) continue;
       const int j = j0 + i;
       *(uint16_t*)(out + body_end + 2 * k) = (uint16_t)j;
-      *(uint32_t*)(out + valoff + 4 * k) = (uint32_t)q[g * nv + j];
+      if (kMask) *(uint32_t*)(out + valoff + 4 * k) = (uint32_t)q[g * nv + j];
       ++k;
     }
   }
@@ -639,6 +698,14 @@ struct Worker {
       if (kMask) {
         if (is_verb(g, j)) {
           const double x = (double)RawBits<Real>::from((uint32_t)q[g * nv + j]);
+          x2 = __dmul_rn(x, x);
+        }
+      } else if (m->vbig[g]) {
+        const int W = nv >> 5;
+        const uint32_t wd = vomask[g * W + (j >> 5)];
+        if ((wd >> (j & 31)) & 1u) {
+          const uint32_t rank = vpre_out[g * W + (j >> 5)] + (uint32_t)__popc(wd & ((1u << (j & 31)) - 1u));
+          const double x = (double)RawBits<Real>::from(*(const uint64_t*)(m->vsec_base[g] + m->vsec_valoff[g] + 8 * rank));
           x2 = __dmul_rn(x, x);
         }
       } else {
@@ -780,9 +847,11 @@ __device__ void Worker<Real>::encode(int g, unsigned long long blk, const PassAr
     const unsigned long long c1 = tid < (nv >> 5) ? (unsigned long long)__popc(vmask[g * (nv >> 5) + tid]) : 0ull;
     nverb_raw = nverb = (int)block_reduce_sum_u64(c1, m->red);
   } else {
-    nverb_raw = vout_cnt[g];
-    nverb = nverb_raw < kVmax ? nverb_raw : kVmax;
+    nverb_raw = nverb = vout_cnt[g];
   }
+  // complex128 with more verbatim values than the lists hold: the section goes straight to
+  // the output like complex64's; the raw values come from a second transform (pass_group)
+  const bool big = !kMask && nverb > kVmax;
   const int C = nv / kChunk;
   // ---- pass 1: statistics and the symbol histogram over this thread's values ----
   // (hash table; runs of equal symbols merged before an insert; inserts stop once the block
@@ -966,7 +1035,7 @@ __device__ void Worker<Real>::encode(int g, unsigned long long blk, const PassAr
   const bool ok = m->ok;
   // complex64: the stream image in shared memory ends with the body; the verbatim section is
   // written straight to the output (it can be as large as the whole block)
-  const uint32_t span = (kMask && mode != kModeConst) ? (uint32_t)pad_to(body_end, 16) : size;
+  const uint32_t span = ((kMask || big) && mode != kModeConst) ? (uint32_t)pad_to(body_end, 16) : size;
   if (ok) {
     for (uint32_t i = tid; i < span / 4; i += T) stage[i] = 0;
     __syncthreads();
@@ -1066,7 +1135,7 @@ __device__ void Worker<Real>::encode(int g, unsigned long long blk, const PassAr
         bw.finish();
       }
       // verbatim section (positions ascending)
-      if (!kMask && nverb > 0) {
+      if (!kMask && nverb > 0 && !big) {
         __syncthreads();
         if (tid == 0) {
           // insertion sort of the (rare) verbatim list by position
@@ -1098,7 +1167,7 @@ __device__ void Worker<Real>::encode(int g, unsigned long long blk, const PassAr
     uint4* dst = (uint4*)(a.out_arena + m->out_off);
     const uint4* src = (const uint4*)stage;
     for (uint32_t i = tid; i < span / 16; i += T) dst[i] = src[i];
-    if (kMask && mode != kModeConst && nverb > 0) {
+    if ((kMask || big) && mode != kModeConst && nverb > 0) {
       for (uint32_t i = span / 16 + tid; i < size / 16; i += T) dst[i] = make_uint4(0u, 0u, 0u, 0u);
       __syncthreads();  // the zero fill lands before the positions and values below
       write_verbatim_inplace(g, a.out_arena + m->out_off, body_end, nverb);
@@ -1131,6 +1200,14 @@ __device__ void Worker<Real>::encode(int g, unsigned long long blk, const PassAr
       bi.maxq_mode = (amax & 0x1FFFFFFFu) | ((unsigned int)mode << 29) | (nverb_raw ? 0x80000000u : 0u);
       a.out_info[blk] = bi;
     }
+  }
+  if (big) {  // values and the verbatim sum follow the second transform
+    if (tid == 0) {
+      m->vbig[g] = 1;
+      m->any_big = 1;
+    }
+    __syncthreads();
+    return;
   }
   const double vs = nverb > 0 ? verbatim_square_tree(g) : 0.0;
   if (tid == 0 && a.vsum) a.vsum[blk] = vs;

@@ -225,13 +225,30 @@ __global__ void __launch_bounds__(256) k_codec_compress(const Real* values, Pass
   if (threadIdx.x == 0) w.m->err = 0;
   for (unsigned long long blk = blockIdx.x; blk < a.ngroups; blk += gridDim.x) {
     __syncthreads();
-    if (threadIdx.x == 0) w.vout_cnt[0] = 0;
-    for (int i = threadIdx.x; i < (L.nv >> 5); i += blockDim.x) w.vmask[i] = 0u;
+    if (threadIdx.x == 0) {
+      w.vout_cnt[0] = 0;
+      w.m->vbig[0] = 0;
+      w.m->any_big = 0;
+      w.m->fix = 0;
+    }
+    for (int i = threadIdx.x; i < (L.nv >> 5); i += blockDim.x) {
+      w.vmask[i] = 0u;
+      w.vomask[i] = 0u;
+    }
     __syncthreads();
     const Real* v = values + blk * (unsigned long long)L.nv;
     for (int j = threadIdx.x; j < L.nv; j += blockDim.x) w.put_value(0, j, v[j]);
     __syncthreads();
     w.encode(0, blk, a);
+    if (w.m->any_big) {  // complex128 with many verbatim values: raw values, then their sum
+      if (threadIdx.x == 0) w.m->fix = 1;
+      __syncthreads();
+      for (int j = threadIdx.x; j < L.nv; j += blockDim.x) w.put_value(0, j, v[j]);
+      __syncthreads();
+      const double vs = w.verbatim_square_tree(0);
+      if (threadIdx.x == 0 && a.vsum) a.vsum[blk] = vs;
+      __syncthreads();
+    }
   }
   if (threadIdx.x == 0 && w.m->err) atomicOr(&a.sc->status, w.m->err);
 }

@@ -247,7 +247,15 @@ __device__ __forceinline__ void pass_group(Worker<Real>& w, const PassArgs& a, c
     blks[g] = bid;
   }
   __syncthreads();
-  if (threadIdx.x < 4) w.vout_cnt[threadIdx.x] = 0;
+  if (threadIdx.x < 4) {
+    w.vout_cnt[threadIdx.x] = 0;
+    w.m->vbig[threadIdx.x] = 0;
+  }
+  if (threadIdx.x == 0) {
+    w.m->any_big = 0;
+    w.m->fix = 0;
+  }
+  for (int i = threadIdx.x; i < a.G * (L.nv >> 5); i += blockDim.x) w.vomask[i] = 0u;  // output verbatim bitmap
   // ---- stream pass-through ----
   // complex128: block slot g keeps the codes of slot src (src = g where the gate acts as the identity on
   // it: the group's high controls are not all 1, or its rows are unit rows; another slot for
@@ -293,6 +301,17 @@ __device__ __forceinline__ void pass_group(Worker<Real>& w, const PassArgs& a, c
       for (int g = 0; g < a.G; ++g) w.pass_through(blks[w.m->pt[g]], blks[g], a);
       return;
     }
+  }
+  // A second round (fix) runs only when a complex128 block stored more verbatim values than
+  // its lists hold: the same decode and transform again, writing just those raw values into
+  // the output streams the first round wrote (every step is deterministic, so the second
+  // round finds the same values).
+  for (int round = 0; round < 2; ++round) {
+  if (round == 1) {
+    __syncthreads();
+    if (!w.m->any_big) break;
+    if (threadIdx.x == 0) w.m->fix = 1;
+    __syncthreads();
   }
   // ---- Decompress(S) ----
   for (int g = 0; g < a.G; ++g) {
@@ -401,10 +420,22 @@ __device__ __forceinline__ void pass_group(Worker<Real>& w, const PassArgs& a, c
     tuple_exact<Real, KM>(w, a, sg, bp, ctrl);
   }
   __syncthreads();
-  // ---- Compress(S) ----
-  for (int g = 0; g < a.G; ++g) {
-    if (any_pt && w.m->pt[g] >= 0) w.pass_through(blks[w.m->pt[g]], blks[g], a);
-    else w.encode(g, blks[g], a);
+  if (round == 0) {
+    // ---- Compress(S) ----
+    for (int g = 0; g < a.G; ++g) {
+      if (any_pt && w.m->pt[g] >= 0) w.pass_through(blks[w.m->pt[g]], blks[g], a);
+      else w.encode(g, blks[g], a);
+    }
+  } else {
+    // the raw values are in place: the verbatim sums of those blocks
+    for (int g = 0; g < a.G; ++g)
+      if (w.m->vbig[g]) {
+        const double vs = w.verbatim_square_tree(g);
+        if (threadIdx.x == 0 && a.vsum) a.vsum[blks[g]] = vs;
+      }
+    __syncthreads();
+    if (threadIdx.x == 0) w.m->fix = 0;
+  }
   }
 }
 

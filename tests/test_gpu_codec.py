@@ -136,13 +136,35 @@ def test_complex64_verbatim_heavy_blocks(sv, b):
         assert d[i * B:(i + 1) * B].tobytes() == oracle.decompress_block(ref, b, oracle.C64, eb).tobytes()
 
 
-def test_verbatim_limit_is_reported(sv):
-    # more than 128 verbatim values in one complex128 block is outside this build's GPU limit
-    b = 8
-    v = np.full(1 << b, 1e7 + 0j)
-    with pytest.raises(sv.SvError) as e:
-        sv.codec_compress(torch.from_numpy(v).cuda(), b, 1e-6)
-    assert e.value.code == sv.ERR_UNSUPPORTED
+@pytest.mark.parametrize("b", [7, 10, 12])
+@pytest.mark.parametrize("kind", ["huge", "ties", "mixed"])
+def test_complex128_verbatim_heavy_blocks(sv, b, kind):
+    # more verbatim values than a block's shared-memory lists hold (128): values beyond the
+    # code range (|x| > 2^29 2eb), values on rounding ties of the grid (2^-6 at eb 1e-6: the
+    # reconstruction error is eb itself, and rounding pushes it past), or three quarters ties
+    B = 1 << b
+    rng = np.random.default_rng(b)
+    eb = 1e-6
+    blocks = []
+    for _ in range(3):
+        if kind == "huge":
+            v = (rng.uniform(1e3, 1e4, B) + 1j * rng.uniform(-1e4, -1e3, B))
+        elif kind == "ties":
+            v = np.full(B, 2.0 ** -6 + 1j * 2.0 ** -6)
+        else:
+            v = rng.standard_normal(B) * 1e-3 + 1j * rng.standard_normal(B) * 1e-3
+            v[np.arange(B) % 4 != 0] = 2.0 ** -6 - 1j * 2.0 ** -6
+        blocks.append(v.astype(np.complex128))
+    refs = [oracle.compress_block(blk, b, oracle.C128, eb) for blk in blocks]
+    assert max(i["n_verbatim"] for _, i in refs) > 128
+    vals = torch.from_numpy(np.concatenate(blocks)).cuda()
+    out, offs, lens, used = sv.codec_compress(vals, b, eb)
+    o, f, l = out.cpu().numpy(), offs.cpu().numpy(), lens.cpu().numpy()
+    for i, (ref, _) in enumerate(refs):
+        assert o[f[i]:f[i] + l[i]].tobytes() == ref, i
+    d = sv.codec_decompress(out, offs, lens, b, oracle.C128, eb).cpu().numpy()
+    for i, (ref, _) in enumerate(refs):
+        assert d[i * B:(i + 1) * B].tobytes() == oracle.decompress_block(ref, b, oracle.C128, eb).tobytes()
 
 
 def test_many_blocks_roundtrip_full_size(sv):

@@ -218,6 +218,17 @@ def test_pass_through_rejects_verbatim_and_rescaled_blocks(sv, pool):
     assert reused > 0
 
 
+@pytest.mark.parametrize("b", [8, 10])
+def test_grover_on_rounding_ties_bit_exact(sv, pool, b):
+    # Grover on 12 qubits at eb 1e-6: the uniform superposition 2^-6 sits on rounding ties of
+    # the 2e-6 grid, so every value is stored verbatim -- far more than the 128 a complex128
+    # block keeps in shared memory. At block_log2 8 the H gates on qubits 8..11 also pair
+    # blocks. Every pass must match the oracle byte for byte.
+    n = 12
+    gates = C.grover(n, C.seeded_index(13, n), 2)
+    run_compare_reuse(sv, pool, n, b, oracle.C128, 1e-6, 0, gates)
+
+
 @pytest.mark.parametrize("threads,compact", [(64, False), (128, False), (256, False), (256, True), (128, True)])
 @pytest.mark.parametrize("dtype", [oracle.C128, oracle.C64])
 def test_launch_shape_does_not_change_results(sv, pool, threads, compact, dtype):
