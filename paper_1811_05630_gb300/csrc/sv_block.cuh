@@ -131,7 +131,8 @@ __host__ __device__ inline int next_pow2(int x) {
   return p;
 }
 
-__host__ __device__ inline Layout make_layout(int b, int G, int csize) {
+// `batch`: the batched pass also keeps the current state's descriptor in shared memory.
+__host__ __device__ inline Layout make_layout(int b, int G, int csize, bool batch = false) {
   Layout L;
   L.nv = 2 << b;
   L.G = G;
@@ -178,19 +179,18 @@ __host__ __device__ inline Layout make_layout(int b, int G, int csize) {
   L.off_fast = o;
   o += (uint32_t)pad_to(sizeof(FastGate), 16);
   L.off_desc = o;  // the batched pass keeps the current state's descriptor here
-  o += (uint32_t)pad_to(sizeof(PassArgs), 16);
+  if (batch) o += (uint32_t)pad_to(sizeof(PassArgs), 16);
   L.off_vmask = o;  // complex64: one bit per value marks a verbatim value kept in place
   o += (uint32_t)pad_to((size_t)G * (L.nv / 32) * 4, 16);
   L.off_vtree = o;  // pairwise verbatim-square tree across threads
   o += 256 * 8;
-  // complex128: output verbatim bitmap, and per-word prefix counts of the input and output
-  // bitmaps (ranks of verbatim values in their stream sections)
+  // complex128: output verbatim bitmap; per-word prefix counts of the input and output
+  // bitmaps (ranks of verbatim values in their stream sections) live in the hash table's
+  // space, which is idle while they are used (decode to transform; the second round)
   L.off_vomask = o;
   o += (uint32_t)pad_to((size_t)G * (L.nv / 32) * 4, 16);
-  L.off_vpre_in = o;
-  o += (uint32_t)pad_to((size_t)G * (L.nv / 32) * 2, 16);
-  L.off_vpre_out = o;
-  o += (uint32_t)pad_to((size_t)G * (L.nv / 32) * 2, 16);
+  L.off_vpre_in = L.off_hkey;
+  L.off_vpre_out = L.off_hkey + (uint32_t)pad_to((size_t)G * (L.nv / 32) * 2, 16);
   L.total = o;
   return L;
 }
@@ -356,7 +356,7 @@ struct Worker {
         if (tid < C) cstart[tid] = cs;
         if (tid == 0) cstart[C] = pbits;
         // decode table: every code of length <= kLutBits fills its 2^(kLutBits-l) entries
-        // with (symbol << 8) | length (never 0: length >= 1)
+        // with (canonical index + 1) << 8 | length (0: longer code)
         for (int i = tid; i < D; i += T) {
           int l = 1;
           while (l < lmax && !(i >= m->offs[l] && i < m->offs[l] + m->lcount[l])) ++l;
@@ -364,7 +364,7 @@ struct Worker {
           if (l <= kLutBits) {
             const uint32_t lo = code << (kLutBits - l), n = 1u << (kLutBits - l);
             if (lo + n <= (1u << kLutBits))
-              for (uint32_t e = 0; e < n; ++e) lut[lo + e] = ((uint32_t)symtab[i] << 8) | (uint32_t)l;
+              for (uint32_t e = 0; e < n; ++e) lut[lo + e] = ((uint32_t)(i + 1) << 8) | (uint32_t)l;
           }
         }
       }
@@ -463,12 +463,11 @@ struct Worker {
       }
       const uint32_t pk = (uint32_t)(buf >> 32);
       const uint32_t e = lut[pk >> (32 - kLutBits)];
-      int sym, l;
-      if (e) {  // short code: symbol and length straight from the table
-        sym = (int)(e >> 8);
+      int idx = -1, l = 0;
+      if (e) {
+        idx = (int)(e >> 8) - 1;
         l = (int)(e & 0xff);
       } else {
-        int idx = -1;
         for (l = kLutBits + 1; l <= lmax; ++l) {
           const int c = (int)(pk >> (32 - l));
           if (m->lcount[l] && c >= m->first[l] && c - m->first[l] < m->lcount[l]) {
@@ -476,15 +475,15 @@ struct Worker {
             break;
           }
         }
-        if (idx < 0 || idx >= D) {
-          cerr = true;
-          break;
-        }
-        sym = symtab[idx];
+      }
+      if (idx < 0 || idx >= D) {
+        cerr = true;
+        break;
       }
       buf <<= l;
       nbuf -= l;
       pos += (uint32_t)l;
+      const int sym = symtab[idx];
       int32_t d;
       if (sym == 0) {
         if (nbuf < 32) {
@@ -656,10 +655,21 @@ struct Worker {
     __syncthreads();
   }
 
+  // complex128 second round: rank of every output verbatim position of block g (per-word
+  // prefix counts of the output bitmap). All threads call it.
+  __device__ void prepare_out_ranks(int g) {
+    const int W = L.nv >> 5;  // <= blockDim.x
+    const uint32_t pc = (int)threadIdx.x < W ? (uint32_t)__popc(vomask[g * W + threadIdx.x]) : 0u;
+    uint32_t tot = 0;
+    const uint32_t pre = block_excl_scan_u32(pc, m->scan, &tot);
+    if ((int)threadIdx.x < W) vpre_out[g * W + threadIdx.x] = (uint16_t)pre;
+    __syncthreads();
+  }
+
   // complex64: write the verbatim section (u16 positions ascending, raw floats) of block g
   // into its stream at `out`, after the zero fill of the section
-  // (complex128 with many verbatim values: positions now; per-word prefix counts and the
-  // section's address kept for the second transform that writes the raw values)
+  // (complex128 with many verbatim values: positions now; the section's address is kept for
+  // the second transform that writes the raw values)
   __device__ void write_verbatim_inplace(int g, uint8_t* out, uint32_t body_end, int nverb) {
     const int tid = threadIdx.x, nv = L.nv, j0 = tid * vpt;
     const uint32_t* bm = kMask ? vmask : vomask;
@@ -668,12 +678,9 @@ struct Worker {
     uint32_t tot = 0;
     uint32_t k = block_excl_scan_u32((uint32_t)__popc(mine), m->scan, &tot);
     const uint32_t valoff = (uint32_t)pad_to(body_end + 2 * nverb, sizeof(Real));
-    if (!kMask) {
-      if ((j0 & 31) == 0) vpre_out[g * (nv >> 5) + (j0 >> 5)] = (uint16_t)k;  // vpt <= 32: word start
-      if (tid == 0) {
-        m->vsec_base[g] = out;
-        m->vsec_valoff[g] = valoff;
-      }
+    if (!kMask && tid == 0) {
+      m->vsec_base[g] = out;
+      m->vsec_valoff[g] = valoff;
     }
     for (int i = 0; i < vpt; ++i) {
       if (!((mine >> i) & 1u)) continue;

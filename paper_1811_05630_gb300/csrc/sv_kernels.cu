@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(256) k_pass_batch(const PassArgs* __restrict__
                                                     const unsigned long long* __restrict__ gprefix,
                                                     int nstates, int b, int Gmax) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const Layout L = make_layout(b, Gmax, (int)sizeof(Real));
+  const Layout L = make_layout(b, Gmax, (int)sizeof(Real), true);
   PassArgs* as = (PassArgs*)(smem + L.off_desc);
   Worker<Real> w;
   QuantP q0{0.0, 0.0, 0.0};
@@ -133,7 +133,7 @@ template <typename Real, int KM>
 static cudaError_t launch_pass_batch_k(const PassArgs* descs, const unsigned long long* gprefix, int nstates,
                                        unsigned long long total_groups, int b, int Gmax, int threads,
                                        cudaStream_t st) {
-  const Layout L = make_layout(b, Gmax, (int)sizeof(Real));
+  const Layout L = make_layout(b, Gmax, (int)sizeof(Real), true);  // the kernel's layout
   static bool configured = false;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(k_pass_batch<Real, KM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
@@ -241,6 +241,7 @@ __global__ void __launch_bounds__(256) k_codec_compress(const Real* values, Pass
     __syncthreads();
     w.encode(0, blk, a);
     if (w.m->any_big) {  // complex128 with many verbatim values: raw values, then their sum
+      w.prepare_out_ranks(0);
       if (threadIdx.x == 0) w.m->fix = 1;
       __syncthreads();
       for (int j = threadIdx.x; j < L.nv; j += blockDim.x) w.put_value(0, j, v[j]);

@@ -173,8 +173,8 @@ __device__ __forceinline__ void tuple_exact(Worker<Real>& w, const PassArgs& a, 
   for (int mm = 0; mm < KM; ++mm) {
     if (mm < a.K) {
       const int p = bp + a.pos_delta[mm];
-      const int g = p / L.nv;
-      const int j = p - g * L.nv;
+      const int g = p >> (w.b + 1);  // block slot (2^(b+1) values per block)
+      const int j = p & (L.nv - 1);
       gs[mm] = g;
       js[mm] = j;
       const Real xr = w.value_at(g, j), xi = w.value_at(g, j + 1);
@@ -230,7 +230,7 @@ __device__ __forceinline__ void tuple_exact(Worker<Real>& w, const PassArgs& a, 
 // One group of 2^h coupled blocks of one state: Decompress, Normalize + GateComputation,
 // Compress (shared by the single-state and the batched pass kernels).
 template <typename Real, int KM>
-__device__ __forceinline__ void pass_group(Worker<Real>& w, const PassArgs& a, const FastGate* fg,
+__device__ __forceinline__ void pass_group(Worker<Real>& w, const PassArgs& a, const FastGate* __restrict__ fg,
                                            double sigma, unsigned long long grp) {
   using A = Arith<Real>;
   const Layout& L = w.L;
@@ -310,6 +310,8 @@ __device__ __forceinline__ void pass_group(Worker<Real>& w, const PassArgs& a, c
   if (round == 1) {
     __syncthreads();
     if (!w.m->any_big) break;
+    for (int g = 0; g < a.G; ++g)
+      if (w.m->vbig[g]) w.prepare_out_ranks(g);
     if (threadIdx.x == 0) w.m->fix = 1;
     __syncthreads();
   }
@@ -340,8 +342,8 @@ __device__ __forceinline__ void pass_group(Worker<Real>& w, const PassArgs& a, c
       for (int mm = 0; mm < KM; ++mm)
         if (mm < a.K) {
           const int p = bp + a.pos_delta[mm];
-          gq[mm] = p / L.nv;
-          jq[mm] = p - gq[mm] * L.nv;
+          gq[mm] = p >> (a.b + 1);
+          jq[mm] = p & (L.nv - 1);
           qv[2 * mm] = w.q[p];
           qv[2 * mm + 1] = w.q[p + 1];
           sentinel |= qv[2 * mm] == kSentinel || qv[2 * mm + 1] == kSentinel;
