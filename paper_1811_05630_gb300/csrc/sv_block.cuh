@@ -104,6 +104,7 @@ struct __align__(16) PassArgs {
 struct FastGate {
   int F;              // fractional bits of W
   int diag;           // the gate matrix is diagonal
+  int real;           // every entry of sigma * G * fl(2eb r) has a zero imaginary part
   long long margin;   // half-width of the band around a rounding tie sent to the exact path
   // outputs that are one input times +-1 (identity rows, permutations, phase +-1 / +-i):
   // source index (member * 2 + component, -1 if not such an output) and sign; their code is
@@ -345,7 +346,6 @@ struct Worker {
           }
           if (idx != D) atomicOr(&m->err, kStCorrupt);
         }
-        for (int i = tid; i < (1 << kLutBits); i += T) lut[i] = 0;
       }
       uint32_t cb = 0;
       if (!bad && tid < C) cb = ((const uint16_t*)(sm + off_chunk))[tid];
@@ -355,17 +355,21 @@ struct Worker {
       if (!bad) {
         if (tid < C) cstart[tid] = cs;
         if (tid == 0) cstart[C] = pbits;
-        // decode table: every code of length <= kLutBits fills its 2^(kLutBits-l) entries
-        // with (canonical index + 1) << 8 | length (0: longer code)
-        for (int i = tid; i < D; i += T) {
-          int l = 1;
-          while (l < lmax && !(i >= m->offs[l] && i < m->offs[l] + m->lcount[l])) ++l;
-          const uint32_t code = (uint32_t)(m->first[l] + (i - m->offs[l]));
-          if (l <= kLutBits) {
-            const uint32_t lo = code << (kLutBits - l), n = 1u << (kLutBits - l);
-            if (lo + n <= (1u << kLutBits))
-              for (uint32_t e = 0; e < n; ++e) lut[lo + e] = ((uint32_t)(i + 1) << 8) | (uint32_t)l;
+        // decode table, one entry per thread step: the kLutBits-bit prefix e starts the code
+        // of length l <= kLutBits whose canonical value is e >> (kLutBits - l) (at most one l
+        // matches: the code is prefix-free); entry (canonical index + 1) << 8 | length, or 0
+        // when the code is longer
+        const int lshort = lmax < kLutBits ? lmax : kLutBits;
+        for (int e = tid; e < (1 << kLutBits); e += T) {
+          uint32_t v = 0;
+          for (int l = 1; l <= lshort; ++l) {
+            const int c = e >> (kLutBits - l);
+            if (c >= m->first[l] && c - m->first[l] < m->lcount[l]) {
+              v = ((uint32_t)(m->offs[l] + c - m->first[l] + 1) << 8) | (uint32_t)l;
+              break;
+            }
           }
+          lut[e] = v;
         }
       }
       __syncthreads();
@@ -375,21 +379,28 @@ struct Worker {
     if (bad && tid == 0) atomicOr(&m->err, kStCorrupt);
     __syncthreads();
     // inverse Lorenzo: q_j = q_{j-2} + delta_j, one running sum per plane (each thread sums
-    // its run, a block scan gives the run's offsets, then a second sweep writes the codes;
-    // the deltas are read twice from shared memory rather than held in registers)
+    // its run held in registers, a block scan gives the run's offsets, then it writes the codes)
     int2 loc = make_int2(0, 0);
-    int32_t* run = qb + tid * vpt;
-    for (int i = 0; i < vpt; i += 2) {
-      loc.x += run[i];
-      loc.y += run[i + 1];
-    }
+    int32_t dv[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i)
+      if (i < vpt) {
+        dv[i] = qb[tid * vpt + i];
+        if (i & 1) loc.y += dv[i];
+        else loc.x += dv[i];
+      }
     int2 off = block_excl_scan_i2(loc, (int2*)m->red);
-    for (int i = 0; i < vpt; i += 2) {
-      off.x += run[i];
-      off.y += run[i + 1];
-      run[i] = off.x;
-      run[i + 1] = off.y;
-    }
+#pragma unroll
+    for (int i = 0; i < 32; ++i)
+      if (i < vpt) {
+        if (i & 1) {
+          off.y += dv[i];
+          qb[tid * vpt + i] = off.y;
+        } else {
+          off.x += dv[i];
+          qb[tid * vpt + i] = off.x;
+        }
+      }
     // verbatim section: ascending positions, then raw values (aligned to the value size)
     if (nverb > nv) {
       if (tid == 0) atomicOr(&m->err, kStCorrupt);

@@ -108,12 +108,13 @@ __device__ inline void fast_prepare(FastGate* fg, const PassArgs& a, double sigm
       fg->ssgn[jj][1] = (int8_t)sg;
     }
   }
-  int diag = 1;
+  int diag = 1, real = 1;
   for (int jj = 0; jj < K; ++jj)
     for (int m = 0; m < K; ++m) {
       const double A = __dmul_rn(a.g[2 * (jj * K + m)], s1);
       const double Bc = __dmul_rn(a.g[2 * (jj * K + m) + 1], s1);
       if (m != jj && (A != 0.0 || Bc != 0.0)) diag = 0;
+      if (Bc != 0.0) real = 0;
       // re += A q_re - B q_im ; im += B q_re + A q_im
       fix(A, &fg->chi[jj][0][m][0], &fg->clo[jj][0][m][0]);
       fix(-Bc, &fg->chi[jj][0][m][1], &fg->clo[jj][0][m][1]);
@@ -121,6 +122,7 @@ __device__ inline void fast_prepare(FastGate* fg, const PassArgs& a, double sigm
       fix(A, &fg->chi[jj][1][m][1], &fg->clo[jj][1][m][1]);
     }
   fg->diag = diag;
+  fg->real = real;
 }
 
 // round(W / 2^F) when it provably equals the exact chain's code; false otherwise
@@ -307,137 +309,145 @@ __device__ __forceinline__ void pass_group(Worker<Real>& w, const PassArgs& a, c
   // the output streams the first round wrote (every step is deterministic, so the second
   // round finds the same values).
   for (int round = 0; round < 2; ++round) {
-  if (round == 1) {
-    __syncthreads();
-    if (!w.m->any_big) break;
-    for (int g = 0; g < a.G; ++g)
-      if (w.m->vbig[g]) w.prepare_out_ranks(g);
-    if (threadIdx.x == 0) w.m->fix = 1;
-    __syncthreads();
-  }
-  // ---- Decompress(S) ----
-  for (int g = 0; g < a.G; ++g) {
-    if (a.input_basis) {
-      const int pos = ((a.basis >> a.b) == blks[g]) ? 2 * (int)(a.basis & (unsigned long long)(B - 1)) : -1;
-      w.load_basis(g, pos);
-    } else if (any_pt && !((w.m->dmask >> g) & 1u)) {
-      w.load_basis(g, -1);  // read by no recoded block: zeros
-    } else {
-      w.decode(g, a.in_arena + a.in_off[blks[g]], a.in_len[blks[g]]);
+    if (round == 1) {
+      __syncthreads();
+      if (!w.m->any_big) break;
+      for (int g = 0; g < a.G; ++g)
+        if (w.m->vbig[g]) w.prepare_out_ranks(g);
+      if (threadIdx.x == 0) w.m->fix = 1;
+      __syncthreads();
     }
-  }
-  // ---- Normalize(S) and GateComputation(G, S), tuple by tuple, in place ----
-  const int ntup = B >> a.nlow;
-  for (int u = threadIdx.x; u < ntup; u += blockDim.x) {
-    unsigned long long o = (unsigned long long)u;
-    for (int l = 0; l < a.nlow; ++l) o = insert_zero_bit(o, a.low_t[l]);
-    const unsigned long long gidx = (blks[0] << a.b) | o;
-    const bool ctrl = a.apply_gate && ((gidx & a.cmask) == a.cmask);
-    const int bp = 2 * (int)o;
-    if (kFast && fg->F >= 0) {
-      int32_t qv[2 * KM];
-      int gq[KM], jq[KM];
-      bool sentinel = false;
-#pragma unroll
-      for (int mm = 0; mm < KM; ++mm)
-        if (mm < a.K) {
-          const int p = bp + a.pos_delta[mm];
-          gq[mm] = p >> (a.b + 1);
-          jq[mm] = p & (L.nv - 1);
-          qv[2 * mm] = w.q[p];
-          qv[2 * mm + 1] = w.q[p + 1];
-          sentinel |= qv[2 * mm] == kSentinel || qv[2 * mm + 1] == kSentinel;
-        }
-      if (!sentinel) {
-        const int F = fg->F;
-        const long long margin = fg->margin;
-        int32_t out[2 * KM];
-        unsigned int exact_mask = 0;
-#pragma unroll
-        for (int jj = 0; jj < KM; ++jj)
-          if (jj < a.K) {
-#pragma unroll
-            for (int p = 0; p < 2; ++p) {
-              // outputs that are +-1 times one input: exact without arithmetic when small
-              const int ssrc = ctrl ? fg->ssrc[jj][p] : 2 * jj + p;
-              bool done = false;
-              if (ssrc >= 0) {
-                int32_t qq = 0;
-#pragma unroll
-                for (int e = 0; e < 2 * KM; ++e)
-                  if (e == ssrc) qq = qv[e];
-                if ((qq < 0 ? -qq : qq) <= fg->qsafe) {
-                  out[2 * jj + p] = (ctrl && fg->ssgn[jj][p] < 0) ? -qq : qq;
-                  done = true;
-                }
-              }
-              if (!done) {
-                long long sh = 0, sl = 0;
-                if (ctrl && fg->diag) {
+    // ---- Decompress(S) ----
+    for (int g = 0; g < a.G; ++g) {
+      if (a.input_basis) {
+        const int pos = ((a.basis >> a.b) == blks[g]) ? 2 * (int)(a.basis & (unsigned long long)(B - 1)) : -1;
+        w.load_basis(g, pos);
+      } else if (any_pt && !((w.m->dmask >> g) & 1u)) {
+        w.load_basis(g, -1);  // read by no recoded block: zeros
+      } else {
+        w.decode(g, a.in_arena + a.in_off[blks[g]], a.in_len[blks[g]]);
+      }
+    }
+    // ---- Normalize(S) and GateComputation(G, S), tuple by tuple, in place ----
+    const int ntup = B >> a.nlow;
+    for (int u = threadIdx.x; u < ntup; u += blockDim.x) {
+      unsigned long long o = (unsigned long long)u;
+      for (int l = 0; l < a.nlow; ++l) o = insert_zero_bit(o, a.low_t[l]);
+      const unsigned long long gidx = (blks[0] << a.b) | o;
+      const bool ctrl = a.apply_gate && ((gidx & a.cmask) == a.cmask);
+      const int bp = 2 * (int)o;
+      if (kFast && fg->F >= 0) {
+        int32_t qv[2 * KM];
+        int gq[KM], jq[KM];
+        bool sentinel = false;
   #pragma unroll
-                  for (int c = 0; c < 2; ++c) {
-                    const long long qq = qv[2 * jj + c];
-                    sh += qq * fg->chi[jj][p][jj][c];
-                    sl += (qq * fg->clo[jj][p][jj][c]) >> 4;
-                  }
-                } else if (ctrl) {
-  #pragma unroll
-                  for (int m = 0; m < KM; ++m)
-                    if (m < a.K) {
-  #pragma unroll
-                      for (int c = 0; c < 2; ++c) {
-                        const long long qq = qv[2 * m + c];
-                        sh += qq * fg->chi[jj][p][m][c];
-                        sl += (qq * fg->clo[jj][p][m][c]) >> 4;
-                      }
-                    }
-                } else {
-                  const long long qq = qv[2 * jj + p];
-                  sh = qq * fg->idhi;
-                  sl = (qq * fg->idlo) >> 4;
-                }
-                if (!fast_round(sh + (sl >> 27), F, margin, &out[2 * jj + p])) exact_mask |= 1u << (2 * jj + p);
-              }
-            }
-          }
-        double zx[2 * KM];
-        if (exact_mask) {
-#pragma unroll
-          for (int e = 0; e < 2 * KM; ++e)
-            if ((exact_mask >> e) & 1u) zx[e] = exact_component(a, sigma, qv, e >> 1, e & 1, ctrl);
-        }
-#pragma unroll
         for (int mm = 0; mm < KM; ++mm)
           if (mm < a.K) {
-#pragma unroll
-            for (int p = 0; p < 2; ++p) {
-              const int e = 2 * mm + p;
-              if ((exact_mask >> e) & 1u) w.put_value(gq[mm], jq[mm] + p, (Real)zx[e]);
-              else w.q[gq[mm] * L.nv + jq[mm] + p] = out[e];
-            }
+            const int p = bp + a.pos_delta[mm];
+            gq[mm] = p >> (a.b + 1);
+            jq[mm] = p & (L.nv - 1);
+            qv[2 * mm] = w.q[p];
+            qv[2 * mm + 1] = w.q[p + 1];
+            sentinel |= qv[2 * mm] == kSentinel || qv[2 * mm + 1] == kSentinel;
           }
-        continue;
+        if (!sentinel) {
+          const int F = fg->F;
+          const long long margin = fg->margin;
+          int32_t out[2 * KM];
+          unsigned int exact_mask = 0;
+  #pragma unroll
+          for (int jj = 0; jj < KM; ++jj)
+            if (jj < a.K) {
+  #pragma unroll
+              for (int p = 0; p < 2; ++p) {
+                // outputs that are +-1 times one input: exact without arithmetic when small
+                const int ssrc = ctrl ? fg->ssrc[jj][p] : 2 * jj + p;
+                bool done = false;
+                if (ssrc >= 0) {
+                  int32_t qq = 0;
+  #pragma unroll
+                  for (int e = 0; e < 2 * KM; ++e)
+                    if (e == ssrc) qq = qv[e];
+                  if ((qq < 0 ? -qq : qq) <= fg->qsafe) {
+                    out[2 * jj + p] = (ctrl && fg->ssgn[jj][p] < 0) ? -qq : qq;
+                    done = true;
+                  }
+                }
+                if (!done) {
+                  long long sh = 0, sl = 0;
+                  if (ctrl && fg->diag) {
+    #pragma unroll
+                    for (int c = 0; c < 2; ++c) {
+                      const long long qq = qv[2 * jj + c];
+                      sh += qq * fg->chi[jj][p][jj][c];
+                      sl += (qq * fg->clo[jj][p][jj][c]) >> 4;
+                    }
+                  } else if (ctrl && fg->real) {  // real matrix: the cross terms are exactly 0
+    #pragma unroll
+                    for (int m = 0; m < KM; ++m)
+                      if (m < a.K) {
+                        const long long qq = qv[2 * m + p];
+                        sh += qq * fg->chi[jj][p][m][p];
+                        sl += (qq * fg->clo[jj][p][m][p]) >> 4;
+                      }
+                  } else if (ctrl) {
+    #pragma unroll
+                    for (int m = 0; m < KM; ++m)
+                      if (m < a.K) {
+    #pragma unroll
+                        for (int c = 0; c < 2; ++c) {
+                          const long long qq = qv[2 * m + c];
+                          sh += qq * fg->chi[jj][p][m][c];
+                          sl += (qq * fg->clo[jj][p][m][c]) >> 4;
+                        }
+                      }
+                  } else {
+                    const long long qq = qv[2 * jj + p];
+                    sh = qq * fg->idhi;
+                    sl = (qq * fg->idlo) >> 4;
+                  }
+                  if (!fast_round(sh + (sl >> 27), F, margin, &out[2 * jj + p])) exact_mask |= 1u << (2 * jj + p);
+                }
+              }
+            }
+          double zx[2 * KM];
+          if (exact_mask) {
+  #pragma unroll
+            for (int e = 0; e < 2 * KM; ++e)
+              if ((exact_mask >> e) & 1u) zx[e] = exact_component(a, sigma, qv, e >> 1, e & 1, ctrl);
+          }
+  #pragma unroll
+          for (int mm = 0; mm < KM; ++mm)
+            if (mm < a.K) {
+  #pragma unroll
+              for (int p = 0; p < 2; ++p) {
+                const int e = 2 * mm + p;
+                if ((exact_mask >> e) & 1u) w.put_value(gq[mm], jq[mm] + p, (Real)zx[e]);
+                else w.q[gq[mm] * L.nv + jq[mm] + p] = out[e];
+              }
+            }
+          continue;
+        }
       }
+      tuple_exact<Real, KM>(w, a, sg, bp, ctrl);
     }
-    tuple_exact<Real, KM>(w, a, sg, bp, ctrl);
-  }
-  __syncthreads();
-  if (round == 0) {
-    // ---- Compress(S) ----
-    for (int g = 0; g < a.G; ++g) {
-      if (any_pt && w.m->pt[g] >= 0) w.pass_through(blks[w.m->pt[g]], blks[g], a);
-      else w.encode(g, blks[g], a);
-    }
-  } else {
-    // the raw values are in place: the verbatim sums of those blocks
-    for (int g = 0; g < a.G; ++g)
-      if (w.m->vbig[g]) {
-        const double vs = w.verbatim_square_tree(g);
-        if (threadIdx.x == 0 && a.vsum) a.vsum[blks[g]] = vs;
-      }
     __syncthreads();
-    if (threadIdx.x == 0) w.m->fix = 0;
-  }
+    if (round == 0) {
+      // ---- Compress(S) ----
+      for (int g = 0; g < a.G; ++g) {
+        if (any_pt && w.m->pt[g] >= 0) w.pass_through(blks[w.m->pt[g]], blks[g], a);
+        else w.encode(g, blks[g], a);
+      }
+    } else {
+      // the raw values are in place: the verbatim sums of those blocks
+      for (int g = 0; g < a.G; ++g)
+        if (w.m->vbig[g]) {
+          const double vs = w.verbatim_square_tree(g);
+          if (threadIdx.x == 0 && a.vsum) a.vsum[blks[g]] = vs;
+        }
+      __syncthreads();
+      if (threadIdx.x == 0) w.m->fix = 0;
+    }
   }
 }
 
