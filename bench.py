@@ -125,21 +125,21 @@ def source_digest() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(workload: str, block_log2: int, threads: int, compact: bool):
-    """DRAM bytes per fused-pass launch from the committed ncu summary, when it was taken on
-    these exact kernel sources and launch configuration; None otherwise."""
+def recorded_traffic(workload: str):
+    """DRAM bytes per fused-pass launch from the committed ncu summary of this workload, when
+    it was taken on these exact kernel sources: (bytes, description of the captured launches),
+    else (None, None)."""
     path = os.path.join(ROOT, "profiles", "k_pass_%s.md" % workload)
     try:
         with open(path) as f:
             for line in f:
                 if line.startswith("TRAFFIC "):
                     kv = dict(x.split("=", 1) for x in line.split()[1:])
-                    if (kv.get("digest") == source_digest() and int(kv.get("b", -1)) == block_log2
-                            and int(kv.get("threads", -1)) == threads and int(kv.get("compact", -1)) == int(compact)):
-                        return float(kv["bytes_per_launch"])
+                    if kv.get("digest") == source_digest():
+                        return float(kv["bytes_per_launch"]), kv.get("launches", "").replace("_", " ")
     except (OSError, ValueError, KeyError):
         pass
-    return None
+    return None, None
 
 
 def peaks():
@@ -325,11 +325,10 @@ def run_ours(args, rank, world, dist):
         pk = peaks()
         kern_s = kern_ms * 1e-3
         achieved = alg_bytes / kern_s / 1e9 if kern_s > 0 else 0.0
-        T = wl.get("threads") or min(256, max(32, (2 << wl["block_log2"]) // 32))
+        traffic, traffic_src = recorded_traffic(wl["name"])
         roof = {"bound": "hbm", "achieved": achieved, "peak": pk.get("hbm_gbs"), "unit": "GB/s",
-                "frac": achieved / pk.get("hbm_gbs", 1.0),
-                "traffic": recorded_traffic(wl["name"], wl["block_log2"], T, bool(wl.get("compact"))),
-                "source_digest": source_digest(),
+                "frac": achieved / pk.get("hbm_gbs", 1.0), "traffic": traffic,
+                "traffic_source": traffic_src, "source_digest": source_digest(),
                 "kernel": "k_pass<double>", "kernel_ms_per_launch": kern_ms / max(npass, 1),
                 "alg_bytes_per_launch": alg_bytes / max(npass, 1),
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "fallback" not in pk else "fallback"}
