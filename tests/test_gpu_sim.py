@@ -320,3 +320,54 @@ def test_fidelity_and_probs_of_compressed_state(sv, pool):
     finally:
         a.close()
         p.close()
+
+
+@pytest.mark.parametrize("b,compact", [(10, True), (11, True), (10, False)])
+def test_grover20_bench_shape_bit_exact(sv, pool, b, compact):
+    # the bench workload at full size (20 qubits, eb 1e-8, complex128) in the launch shapes the
+    # autotuner picks: every block stream and the stored norm equal the oracle's after the H
+    # layer and after 60 more gates of the dense stage
+    n = 20
+    gates = C.grover(n, C.seeded_index(11, n))[:80]
+    st = sv.State(pool, n, 14, 1e-8, oracle.C128, block_log2=b)
+    try:
+        st.set_threads(256)
+        st.set_compact(compact)
+        st.reset_basis(0)
+        cs = oracle.CompressedSim(n, 14, b, oracle.C128, 1e-8, 0)
+        for i, g in enumerate(gates):
+            st.apply(g.matrix, g.targets, g.controls)
+            cs.apply(g.matrix, g.targets, g.controls)
+            if i + 1 in (20, 50, 80):
+                assert_same_state(st, cs, "gate %d" % i)
+    finally:
+        st.close()
+
+
+def test_qft30_full_size_properties(sv):
+    # 30 qubits (16 GiB uncompressed), the QFT34 path at a size the test box holds: the oracle
+    # cannot run it, so properties that hold at any size are checked -- the fidelity against
+    # the closed form within the first-order error model (fresh quantization adds about
+    # (2/3) eb^2 per value over ~2.5 2^n values; 4x margin), |psi|^2 of sampled amplitudes at
+    # 2^-n, a stored norm of 1 within the same error
+    n, eb = 30, 1e-7
+    x = C.seeded_index(0, n)
+    pool = sv.Pool(24 << 30)
+    st = sv.State(pool, n, 24, eb, oracle.C128, block_log2=11)
+    try:
+        st.set_threads(256)
+        st.set_compact(True)
+        st.reset_basis(x)
+        st.run(C.qft(n))
+        f = st.fidelity_qft(x)
+        model = 2.5 * 2.0 ** n * (2.0 / 3.0) * eb * eb
+        assert 1.0 - f < 4 * model, (1.0 - f, model)
+        idx = np.random.default_rng(3).integers(0, 1 << n, size=4000, dtype=np.uint64)
+        amps = st.amplitudes(idx)
+        ratio = np.abs(amps) ** 2 / st.norm() * 2.0 ** n
+        assert abs(ratio.mean() - 1.0) < 0.01 and ratio.std() < 0.1
+        assert abs(st.norm() - 1.0) < 1e-3
+        assert st.stats()["replayed_passes"] < 16
+    finally:
+        st.close()
+        pool.close()
