@@ -79,6 +79,12 @@ def _load():
         L.orc_compress_block.restype = sz
         L.orc_decompress_block.argtypes = [vp, sz, i, i, d, vp]
         L.orc_decompress_block.restype = i
+        L.orc_compress_block_k.argtypes = [vp, i, i, d, i, vp, ctypes.POINTER(_BlockInfo)]
+        L.orc_compress_block_k.restype = sz
+        L.orc_decompress_block_k.argtypes = [vp, sz, i, i, d, i, vp]
+        L.orc_decompress_block_k.restype = i
+        L.orc_csim_create_k.argtypes = [i, i, i, i, d, u64, i]
+        L.orc_csim_create_k.restype = vp
         L.orc_huffman_lengths.argtypes = [vp, vp, i, vp]
         L.orc_huffman_lengths.restype = i
         L.orc_plain_apply.argtypes = [vp, i, i, vp, vp, i, vp, i]
@@ -114,25 +120,26 @@ def block_bound(block_log2: int, dtype: int) -> int:
     return int(_load().orc_block_bound(block_log2, dtype))
 
 
-def compress_block(values: np.ndarray, block_log2: int, dtype: int, eb: float):
-    """Compress 2^block_log2 complex amplitudes; returns (stream bytes, info dict)."""
+def compress_block(values: np.ndarray, block_log2: int, dtype: int, eb: float, chunk: int = 32):
+    """Compress 2^block_log2 complex amplitudes; returns (stream bytes, info dict). `chunk`:
+    Huffman symbols per stored chunk bit count (16, 32 or 64)."""
     L = _load()
     v = np.ascontiguousarray(values, dtype=_cdtype(dtype))
     assert v.size == 1 << block_log2
     out = np.zeros(block_bound(block_log2, dtype), dtype=np.uint8)
     info = _BlockInfo()
-    n = L.orc_compress_block(_ptr(v), block_log2, dtype, eb, _ptr(out), ctypes.byref(info))
+    n = L.orc_compress_block_k(_ptr(v), block_log2, dtype, eb, chunk, _ptr(out), ctypes.byref(info))
     if n == 0:
         raise ValueError("orc_compress_block rejected its arguments")
     d = {f: getattr(info, f) for f, _ in _BlockInfo._fields_}
     return out[:n].tobytes(), d
 
 
-def decompress_block(stream: bytes, block_log2: int, dtype: int, eb: float) -> np.ndarray:
+def decompress_block(stream: bytes, block_log2: int, dtype: int, eb: float, chunk: int = 32) -> np.ndarray:
     L = _load()
     buf = np.frombuffer(stream, dtype=np.uint8).copy()
     out = np.zeros(1 << block_log2, dtype=_cdtype(dtype))
-    rc = L.orc_decompress_block(_ptr(buf), buf.size, block_log2, dtype, eb, _ptr(out))
+    rc = L.orc_decompress_block_k(_ptr(buf), buf.size, block_log2, dtype, eb, chunk, _ptr(out))
     if rc != 0:
         raise ValueError("malformed block stream (%d)" % rc)
     return out
@@ -180,10 +187,12 @@ class PlainSim:
 class CompressedSim:
     """O2: Algorithm 1 over a block-compressed state (see sv_oracle.c)."""
 
-    def __init__(self, n: int, slice_log2: int, block_log2: int, dtype: int, eb: float, basis_index: int = 0):
+    def __init__(self, n: int, slice_log2: int, block_log2: int, dtype: int, eb: float, basis_index: int = 0,
+                 chunk: int = 32):
         self.n, self.slice_log2, self.block_log2, self.dtype, self.eb = n, slice_log2, block_log2, dtype, eb
+        self.chunk = chunk
         self._L = _load()
-        self._h = self._L.orc_csim_create(n, slice_log2, block_log2, dtype, eb, basis_index)
+        self._h = self._L.orc_csim_create_k(n, slice_log2, block_log2, dtype, eb, basis_index, chunk)
         if not self._h:
             raise ValueError("orc_csim_create rejected its arguments")
 

@@ -28,7 +28,7 @@ typedef unsigned __int128 u128;
 #define HDR_BYTES 16
 #define SYM_RADIUS 32767   /* |delta| <= 32767 maps to symbol delta + 32768 */
 #define SYM_ESCAPE 0       /* symbol 0: delta follows as 32 raw bits */
-#define CHUNK_SYMS 32      /* symbols per decode chunk */
+#define CHUNK_DEFAULT 32   /* symbols per decode chunk unless the caller picks 16 or 64 */
 #define HUFF_MAX_DISTINCT 256
 #define Q_LIMIT 536870912.0 /* 2^29: |x*r| must be below this to be quantized */
 
@@ -231,9 +231,17 @@ static int bit_width(uint32_t z) {
   return w;
 }
 
+static int chunk_ok(int chunk) { return chunk == 16 || chunk == 32 || chunk == 64; }
+
 size_t orc_compress_block(const void* values, int block_log2, int dtype, double eb,
                           uint8_t* out, orc_block_info* info) {
-  if (block_log2 < 5 || block_log2 > 12 || !(eb > 0) || (dtype != ORC_C64 && dtype != ORC_C128))
+  return orc_compress_block_k(values, block_log2, dtype, eb, CHUNK_DEFAULT, out, info);
+}
+
+size_t orc_compress_block_k(const void* values, int block_log2, int dtype, double eb, int chunk,
+                            uint8_t* out, orc_block_info* info) {
+  if (block_log2 < 5 || block_log2 > 12 || !(eb > 0) || (dtype != ORC_C64 && dtype != ORC_C128) ||
+      !chunk_ok(chunk))
     return 0;
   const size_t B = (size_t)1 << block_log2;
   const size_t nv = 2 * B; /* values in the block: re, im interleaved */
@@ -316,7 +324,7 @@ size_t orc_compress_block(const void* values, int block_log2, int dtype, double 
     uint32_t* syms = NULL;
     int Lmax = 0;
     uint64_t payload_bits = 0;
-    size_t nchunks = nv / CHUNK_SYMS;
+    size_t nchunks = nv / (size_t)chunk;
     size_t huff_body = 0;
     if (D <= HUFF_MAX_DISTINCT) {
       syms = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)D);
@@ -381,7 +389,7 @@ size_t orc_compress_block(const void* values, int block_log2, int dtype, double 
       uint64_t pos = 0;
       for (size_t ch = 0; ch < nchunks; ++ch) {
         uint64_t start = pos;
-        for (size_t j = ch * CHUNK_SYMS; j < (ch + 1) * CHUNK_SYMS; ++j) {
+        for (size_t j = ch * (size_t)chunk; j < (ch + 1) * (size_t)chunk; ++j) {
           pos += (uint64_t)len_of[symb[j]];
           if (symb[j] == SYM_ESCAPE) pos += 32;
         }
@@ -438,7 +446,12 @@ size_t orc_compress_block(const void* values, int block_log2, int dtype, double 
 
 int orc_decompress_block(const uint8_t* in, size_t len, int block_log2, int dtype, double eb,
                          void* values_out) {
-  if (len < HDR_BYTES) return -1;
+  return orc_decompress_block_k(in, len, block_log2, dtype, eb, CHUNK_DEFAULT, values_out);
+}
+
+int orc_decompress_block_k(const uint8_t* in, size_t len, int block_log2, int dtype, double eb,
+                           int chunk, void* values_out) {
+  if (len < HDR_BYTES || !chunk_ok(chunk)) return -1;
   const size_t B = (size_t)1 << block_log2;
   const size_t nv = 2 * B;
   quant_params p = qparams(eb, dtype);
@@ -481,7 +494,7 @@ int orc_decompress_block(const uint8_t* in, size_t len, int block_log2, int dtyp
       ptr += pad_to(2 * (size_t)Lmax, 4);
       const uint8_t* symtab = ptr;
       ptr += pad_to(2 * (size_t)D, 4);
-      size_t nchunks = nv / CHUNK_SYMS;
+      size_t nchunks = nv / (size_t)chunk;
       ptr += pad_to(2 * nchunks, 4);
       /* canonical decoding: first code and first index of every length */
       uint32_t first[34];
@@ -680,7 +693,7 @@ void orc_plain_apply(void* state, int n, int dtype, const double* G, const int* 
  * 2^(slice_log2 - block_log2) independently coded blocks.
  * ---------------------------------------------------------------------------------- */
 struct orc_csim {
-  int n, slice_log2, block_log2, dtype;
+  int n, slice_log2, block_log2, dtype, chunk;
   double eb;
   quant_params qp;
   uint64_t nblocks;
@@ -719,7 +732,7 @@ static double stored_norm(const orc_csim* s) {
 static void set_block(orc_csim* s, uint64_t b, const void* vals) {
   size_t bound = orc_block_bound(s->block_log2, s->dtype);
   uint8_t* tmp = (uint8_t*)malloc(bound);
-  size_t len = orc_compress_block(vals, s->block_log2, s->dtype, s->eb, tmp, &s->infos[b]);
+  size_t len = orc_compress_block_k(vals, s->block_log2, s->dtype, s->eb, s->chunk, tmp, &s->infos[b]);
   free(s->streams[b]);
   s->streams[b] = (uint8_t*)malloc(len);
   memcpy(s->streams[b], tmp, len);
@@ -729,8 +742,14 @@ static void set_block(orc_csim* s, uint64_t b, const void* vals) {
 
 orc_csim* orc_csim_create(int n, int slice_log2, int block_log2, int dtype, double eb,
                           uint64_t basis_index) {
+  return orc_csim_create_k(n, slice_log2, block_log2, dtype, eb, basis_index, CHUNK_DEFAULT);
+}
+
+orc_csim* orc_csim_create_k(int n, int slice_log2, int block_log2, int dtype, double eb,
+                            uint64_t basis_index, int chunk) {
   if (n < block_log2 || slice_log2 < block_log2 || slice_log2 > n || block_log2 < 5 ||
-      block_log2 > 12 || !(eb > 0) || (dtype != ORC_C64 && dtype != ORC_C128) || n > 40)
+      block_log2 > 12 || !(eb > 0) || (dtype != ORC_C64 && dtype != ORC_C128) || n > 40 ||
+      !chunk_ok(chunk))
     return NULL;
   if (basis_index >> n) return NULL;
   orc_csim* s = (orc_csim*)calloc(1, sizeof(orc_csim));
@@ -738,6 +757,7 @@ orc_csim* orc_csim_create(int n, int slice_log2, int block_log2, int dtype, doub
   s->slice_log2 = slice_log2;
   s->block_log2 = block_log2;
   s->dtype = dtype;
+  s->chunk = chunk;
   s->eb = eb;
   s->qp = qparams(eb, dtype);
   s->nblocks = (uint64_t)1 << (n - block_log2);
@@ -783,8 +803,8 @@ void orc_csim_read(const orc_csim* s, void* out) {
   size_t B = (size_t)1 << s->block_log2;
   size_t cs = (size_t)comp_size(s->dtype);
   for (uint64_t b = 0; b < s->nblocks; ++b)
-    orc_decompress_block(s->streams[b], s->lens[b], s->block_log2, s->dtype, s->eb,
-                         (uint8_t*)out + b * 2 * B * cs);
+    orc_decompress_block_k(s->streams[b], s->lens[b], s->block_log2, s->dtype, s->eb, s->chunk,
+                           (uint8_t*)out + b * 2 * B * cs);
 }
 
 void orc_csim_load(orc_csim* s, const void* values) {
@@ -839,8 +859,8 @@ int orc_csim_apply(orc_csim* s, const double* G, const int* targets, int k, cons
     for (int g = 0; g < G_; ++g)
       for (size_t bi = 0; bi < S / B; ++bi) {
         uint64_t blk = (slice_ids[g] << (sl - bl)) + bi;
-        orc_decompress_block(s->streams[blk], s->lens[blk], bl, s->dtype, s->eb,
-                             buf + ((size_t)g * S + bi * B) * 2 * cs);
+        orc_decompress_block_k(s->streams[blk], s->lens[blk], bl, s->dtype, s->eb, s->chunk,
+                               buf + ((size_t)g * S + bi * B) * 2 * cs);
       }
     /* Normalize(S) */
     for (size_t e = 0; e < (size_t)G_ * S * 2; ++e) {
@@ -896,8 +916,8 @@ int orc_csim_apply(orc_csim* s, const double* G, const int* targets, int k, cons
     for (int g = 0; g < G_; ++g)
       for (size_t bi = 0; bi < S / B; ++bi) {
         uint64_t blk = (slice_ids[g] << (sl - bl)) + bi;
-        size_t len = orc_compress_block(buf + ((size_t)g * S + bi * B) * 2 * cs, bl, s->dtype,
-                                        s->eb, tmp, &new_infos[blk]);
+        size_t len = orc_compress_block_k(buf + ((size_t)g * S + bi * B) * 2 * cs, bl, s->dtype,
+                                          s->eb, s->chunk, tmp, &new_infos[blk]);
         new_streams[blk] = (uint8_t*)malloc(len);
         memcpy(new_streams[blk], tmp, len);
         new_lens[blk] = len;

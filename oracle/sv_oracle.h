@@ -59,6 +59,13 @@ size_t orc_compress_block(const void* values, int block_log2, int dtype, double 
 int orc_decompress_block(const uint8_t* stream, size_t len, int block_log2, int dtype,
                          double eb, void* values_out);
 
+/* The same with the Huffman decode-chunk size (symbols per stored chunk bit count: 16, 32 or
+ * 64; the functions above use 32). It changes the bytes of HUFF streams. */
+size_t orc_compress_block_k(const void* values, int block_log2, int dtype, double eb, int chunk,
+                            uint8_t* out, orc_block_info* info);
+int orc_decompress_block_k(const uint8_t* stream, size_t len, int block_log2, int dtype,
+                           double eb, int chunk, void* values_out);
+
 /* Huffman code lengths by the two-queue method (leaves sorted by frequency, then symbol;
  * ties between queue heads go to the leaf). freq[i] > 0 for i < n; lens_out[i] receives
  * the length of symbol i. Exposed for tests. Returns the maximum length. */
@@ -75,6 +82,8 @@ void orc_plain_apply(void* state, int n, int dtype, const double* G, const int* 
 typedef struct orc_csim orc_csim;
 orc_csim* orc_csim_create(int n, int slice_log2, int block_log2, int dtype, double eb,
                           uint64_t basis_index);
+orc_csim* orc_csim_create_k(int n, int slice_log2, int block_log2, int dtype, double eb,
+                            uint64_t basis_index, int chunk);
 void orc_csim_destroy(orc_csim* s);
 /* One gate pass over every slice. Returns 0, or -1 on an argument error, -2 when the
  * stored norm collapses to zero or is not finite. */

@@ -155,7 +155,7 @@ def test_huffman_tie_break_leaf_first():
     assert list(L) == [2, 2, 2, 2]
 
 
-def parse_stream(s, b, dtype):
+def parse_stream(s, b, dtype, chunk=32):
     mode, dt, bl, param, nverb, D = struct.unpack_from("<BBBBHH", s, 0)
     assert dt == dtype and bl == b
     out = dict(mode=mode, param=param, nverb=nverb, D=D)
@@ -167,10 +167,11 @@ def parse_stream(s, b, dtype):
         off += (2 * param + 3) // 4 * 4
         syms = struct.unpack_from("<%dH" % D, s, off)
         off += (2 * D + 3) // 4 * 4
-        C = (2 << b) // 32
+        C = (2 << b) // chunk
         chunks = struct.unpack_from("<%dH" % C, s, off)
+        off += (2 * C + 3) // 4 * 4
         assert sum(chunks) == pbits
-        out.update(counts=counts, syms=syms, pbits=pbits)
+        out.update(counts=counts, syms=syms, pbits=pbits, chunks=chunks, payload_off=off)
     return out
 
 
@@ -225,3 +226,45 @@ def test_round_half_even_ties():
     # ties go to the even code, and |x - x'| == eb exactly is within the bound
     assert info["n_verbatim"] == 0
     assert d[0] == 2 * two + 4j * two and d[1] == -2 * two - 0j
+
+
+@pytest.mark.parametrize("chunk", [16, 32, 64])
+@pytest.mark.parametrize("kind,eb", [("qft", 1e-4), ("walsh", 1e-6), ("normal", 1e-4), ("grover", 1e-6)])
+def test_chunk_table_matches_an_independent_decode(chunk, kind, eb):
+    # the Huffman chunk size only changes the table of per-chunk bit counts: decode the payload
+    # bit by bit with the canonical code (written here from the stored counts and symbols) and
+    # check every stored count is the bits its `chunk` symbols take (32 more per escape), and
+    # the reconstruction is the same for every chunk size
+    b = 10
+    rng = np.random.default_rng(11)
+    v = gen_block(kind, b, rng, oracle.C128)
+    v[::97] += 0.5  # a few large jumps: escapes
+    s, info = oracle.compress_block(v, b, oracle.C128, eb, chunk=chunk)
+    p = parse_stream(s, b, oracle.C128, chunk=chunk)
+    assert p["mode"] == oracle.MODE_HUFF
+    code_of = {}
+    code, prev, i = 0, None, 0
+    for L, c in enumerate(p["counts"], start=1):
+        for _ in range(c):
+            if prev is not None:
+                code = (code + 1) << (L - prev)
+            code_of[(code, L)] = p["syms"][i]
+            prev = L
+            i += 1
+    words = struct.unpack_from("<%dI" % ((p["pbits"] + 31) // 32), s, p["payload_off"])
+    bits = "".join(format(w, "032b") for w in words)
+    pos = 0
+    for ci, stored in enumerate(p["chunks"]):
+        start = pos
+        for _ in range(chunk):
+            L = 1
+            while (int(bits[pos:pos + L], 2), L) not in code_of:
+                L += 1
+                assert L <= 24
+            sym = code_of[(int(bits[pos:pos + L], 2), L)]
+            pos += L + (32 if sym == 0 else 0)
+        assert pos - start == stored, ci
+    assert pos == p["pbits"]
+    base = oracle.decompress_block(oracle.compress_block(v, b, oracle.C128, eb)[0], b, oracle.C128, eb)
+    got = oracle.decompress_block(s, b, oracle.C128, eb, chunk=chunk)
+    assert got.tobytes() == base.tobytes()
