@@ -266,6 +266,7 @@ def run_ours(args, rank, world, dist):
         wl["block_log2"] = tuned["block_log2"]
         wl["threads"] = tuned["threads"]
         wl["compact"] = tuned["compact"]
+        wl["chunk"] = tuned["chunk"]
     i0 = start_of_dense_stage(wl)
     need = args.warmup + args.steps
     assert i0 + need <= len(gates), "not enough gates for the requested steps"
@@ -273,6 +274,8 @@ def run_ours(args, rank, world, dist):
         wl["threads"] = args.threads
     if args.compact:
         wl["compact"] = True
+    if args.chunk:
+        wl["chunk"] = args.chunk
     pool_bytes = int(args.pool_gb * (1 << 30))
     pool = sv.Pool(pool_bytes)
     arena = args.arena_mb << 20
@@ -288,6 +291,8 @@ def run_ours(args, rank, world, dist):
     if wl.get("threads"):
         st.set_threads(wl["threads"])
     st.set_compact(bool(wl.get("compact")))
+    if wl.get("chunk", 32) != 32:
+        st.set_chunk(wl["chunk"])
     st.reset_basis(wl["basis"])
     st.run(gates[:i0])
     for g in gates[i0:i0 + args.warmup]:
@@ -398,7 +403,8 @@ def run_ours(args, rank, world, dist):
             "data": "synthetic",
             "config": {"workload": wl["desc"], "block_log2": wl["block_log2"],
                        "threads_per_cta": wl.get("threads") or "default",
-                       "register_capped_build": bool(wl.get("compact")), "autotune": tuned,
+                       "register_capped_build": bool(wl.get("compact")), "huffman_chunk": wl.get("chunk", 32),
+                       "autotune": tuned,
                        "arena_bytes": arena, "replayed_passes_in_timed_region": replays,
                        "parallelism": "replicas",
                        "l2": "flushed between timed steps (512 MiB write, untimed); compressed state %d B"
@@ -453,6 +459,8 @@ def run_full_circuit(args):
     if args.threads:
         st.set_threads(args.threads)
     st.set_compact(args.compact)
+    if args.chunk and args.chunk != 32:
+        st.set_chunk(args.chunk)
     st.reset_basis(wl["basis"])
     st.sync()
     raw = (16 if wl["dtype"] == 2 else 8) << n
@@ -488,7 +496,7 @@ def run_full_circuit(args):
     res = {
         "workload": wl["desc"], "dtype": wl["dtype"], "eb": wl["eb"],
         "block_log2": wl["block_log2"], "threads_per_cta": args.threads or "default",
-        "register_capped_build": args.compact,
+        "register_capped_build": args.compact, "huffman_chunk": args.chunk or 32,
         "gates": len(gates), "blocks_reused_fraction": reused / (len(gates) * stt["n_blocks"]),
         "replayed_passes": stt["replayed_passes"],
         "amp_updates_per_s_wall": (1 << n) * len(gates) / wall,
@@ -596,6 +604,7 @@ def main():
     ap.add_argument("--block-log2", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0, help="CTA size of the fused pass (0: tuned/default)")
     ap.add_argument("--compact", action="store_true", help="register-capped build of the fused pass")
+    ap.add_argument("--chunk", type=int, default=0, help="Huffman chunk size (16, 32, 64; 0: tuned/32)")
     ap.add_argument("--eb", type=float, default=0.0, help="override the workload's error bound (full-circuit mode)")
     ap.add_argument("--dtype", choices=["c128", "c64"], default=None, help="override the workload's dtype (full-circuit mode)")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",

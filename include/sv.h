@@ -174,9 +174,10 @@ int sv_stats(sv_state* s, sv_stats_t* out);
 
 /* Threads per CTA of the fused pass for this state (an autotuning knob; the paper has no
  * counterpart): 0 restores the default (one thread per 32-value decode chunk, 32..256);
- * otherwise a power of two T, 32 <= T <= 256, with 2 <= 2^(block_log2+1) / T <= 32.
- * Results (streams, norms) do not depend on it. SV_ERR_ARG for other values or a plain
- * state. A batch runs with the setting of its first state. */
+ * otherwise a power of two T, 32 <= T <= 256, with 2 <= 2^(block_log2+1) / T <= 32 and
+ * 2^(block_log2+1) / chunk <= T (sv_set_chunk). Results (streams, norms) do not depend on
+ * it. SV_ERR_ARG for other values or a plain state. A batch runs with the setting of its
+ * first state. */
 int sv_set_threads(sv_state* s, int threads);
 
 /* Select (on != 0) the register-capped build of the fused pass for 1- and 2-qubit gates
@@ -184,6 +185,14 @@ int sv_set_threads(sv_state* s, int threads);
  * default build). An autotuning knob with no counterpart in the paper; results do not
  * depend on it. SV_ERR_ARG for a plain state. Batches ignore it. */
 int sv_set_compact(sv_state* s, int on);
+
+/* Huffman chunk size of the state's block format: the number of symbols per stored chunk bit
+ * count, each chunk decoded by one thread (16, 32 or 64; the default 32). Smaller chunks
+ * decode with more threads in parallel and cost 16 more bits per chunk of stream. It changes
+ * the bytes of the streams (not the decoded values), so the state is reset to |0...0>
+ * (synchronizing). Needs 2^(block_log2+1) / chunk <= the state's CTA size (sv_set_threads),
+ * SV_ERR_ARG otherwise; batched states must share it. An autotuning knob. */
+int sv_set_chunk(sv_state* s, int chunk);
 int sv_norm(sv_state* s, double* out);
 
 /* Overlap with the exact QFT of the basis state |x> (the closed form

@@ -132,6 +132,7 @@ struct sv_state {
   unsigned long long replayed = 0;  // passes re-run after an arena overflow
   int threads = 0;                  // CTA size of the fused pass (0: default)
   bool compact = false;             // register-capped build of the pass (1- and 2-qubit gates)
+  int huff_chunk = 32;              // Huffman chunk size of the block format
   // passes between status checks (an overflow poisons every later pass until the check
   // replays them): about 2 ms of device work, 1 after an overflow
   int sync_every = 16;
@@ -207,6 +208,7 @@ void build_args(const sv_state* s, const Logged& lg, PassArgs& a) {
   a.out_off = s->toff[lg.out_id];
   a.out_len = s->tlen[lg.out_id];
   a.threads = s->threads;
+  a.chunk = s->huff_chunk;
   a.in_info = s->binfo[lg.in_id];
   a.out_info = s->binfo[lg.out_id];
   for (int g = 0; g < 4; ++g) a.pt_src[g] = -1;
@@ -691,8 +693,18 @@ int sv_norm(sv_state* s, double* out) {
 
 int sv_set_threads(sv_state* s, int threads) {
   if (!s || s->plain || (threads != 0 && !threads_ok(s->b, threads))) return SV_ERR_ARG;
+  if (!chunk_ok(s->b, s->huff_chunk, threads ? threads : worker_threads(s->b))) return SV_ERR_ARG;
   s->threads = threads;
   return SV_OK;
+}
+
+int sv_set_chunk(sv_state* s, int chunk) {
+  if (!s || s->plain) return SV_ERR_ARG;
+  if (!chunk_ok(s->b, chunk, s->threads ? s->threads : worker_threads(s->b))) return SV_ERR_ARG;
+  int rc = sv_sync(s);
+  if (rc) return rc;
+  s->huff_chunk = chunk;
+  return sv_reset_basis(s, 0);  // the stored streams were coded with the old chunk size
 }
 
 int sv_set_compact(sv_state* s, int on) {
@@ -984,7 +996,7 @@ int sv_batch_apply(sv_batch* bt, sv_state* const* states, const sv_gate_t* gates
   for (int i = 0; i < count; ++i) {
     const sv_state* s = states[i];
     const sv_gate_t& g = gates[i];
-    if (!s || s->plain || s->dtype != s0->dtype || s->b != s0->b || s->st != bt->st || !g.G ||
+    if (!s || s->plain || s->dtype != s0->dtype || s->b != s0->b || s->huff_chunk != s0->huff_chunk || s->st != bt->st || !g.G ||
         !gate_args_ok(s, g.targets, g.k, g.controls, g.n_controls))
       return SV_ERR_ARG;
     for (int j = 0; j < i; ++j)
@@ -1026,7 +1038,7 @@ int sv_batch_apply(sv_batch* bt, sv_state* const* states, const sv_gate_t* gates
     cudaError_t r = cudaMemcpyAsync(bt->d_blob, src, bt->blob_bytes, cudaMemcpyHostToDevice, bt->st);
     if (r == cudaSuccess)
       r = launch_pass_batch(d_descs, d_prefix, count, hp[count], s0->b, gmax, kbucket,
-                            s0->dtype == SV_C64 ? 1 : 2, s0->threads, bt->st);
+                            s0->dtype == SV_C64 ? 1 : 2, s0->threads, s0->huff_chunk, bt->st);
     if (r == cudaSuccess) r = launch_norm_batch(d_descs, count, bt->st);
     return r;
   };

@@ -85,6 +85,7 @@ struct __align__(16) PassArgs {
   double* tree;  // scratch of the norm kernel's verbatim-sum tree (2 (nblocks / 256 + 1) doubles)
   unsigned int seq;
   int threads;  // CTA size (0: worker_threads(b)); results do not depend on it
+  int chunk;    // Huffman chunk size (0: 32); 2^(b+1) / chunk <= CTA size
   // stream pass-through: pt_ok bit 0 re-emits blocks whose inputs are all zero, bit 1
   // (complex128) blocks whose rows are unit rows: slot g of a group whose high controls are
   // all 1 takes the codes of slot pt_src[g] (-1: never); need[g] is the mask of the slots
@@ -171,7 +172,7 @@ __host__ __device__ inline Layout make_layout(int b, int G, int csize, bool batc
   L.sort_off = L.off_lens2 + (uint32_t)pad_to(2 * L.dcap, 4);
   L.sort_n = L.dcap < 256 ? L.dcap : 256;
   uint32_t build = L.sort_off + (uint32_t)(8 * L.sort_n);
-  uint32_t dec = (uint32_t)(4 * (1 << kLutBits) + 4 * (L.nv / kChunk + 1));
+  uint32_t dec = (uint32_t)(4 * (1 << kLutBits) + 4 * (L.nv / kChunkMin + 1));
   L.build_bytes = (uint32_t)pad_to(build > dec ? build : dec, 16);
   L.off_build = o;
   o += L.build_bytes;
@@ -203,9 +204,14 @@ __host__ __device__ inline bool threads_ok(int b, int t) {
   const int nv = 2 << b;
   return t >= 32 && t <= 256 && (t & (t - 1)) == 0 && nv / t >= 2 && nv / t <= 32;
 }
+// Huffman chunk size `chunk` works with CTA size T when every chunk has its decoding thread
+// and spans whole threads' value runs: 2^(b+1) / chunk <= T.
+__host__ __device__ inline bool chunk_ok(int b, int chunk, int t) {
+  return (chunk == 16 || chunk == 32 || chunk == 64) && (2 << b) / chunk <= t;
+}
 __host__ __device__ inline int worker_threads(int b) {
   int nv = 2 << b;
-  int t = nv / kChunk;
+  int t = nv / kChunkDefault;
   if (t > 256) t = 256;
   if (t < 32) t = 32;
   return t;
@@ -215,6 +221,7 @@ template <typename Real>
 struct Worker {
   Layout L;
   int T, vpt, b;
+  int kc;  // Huffman chunk size of the state (symbols per stored chunk bit count)
   QuantP qp;
   int32_t* q;
   uint16_t *vin_pos, *vout_pos;
@@ -236,6 +243,7 @@ struct Worker {
     b = b_;
     T = blockDim.x;
     vpt = L.nv / T;
+    kc = kChunkDefault;
     qp = p;
     q = (int32_t*)(smem + L.off_q);
     vin_bits = (uint64_t*)(smem + L.off_vin_bits);
@@ -322,7 +330,7 @@ struct Worker {
       }
     } else if (!bad && mode == kModeHuff) {
       const int lmax = param;
-      const int C = nv / kChunk;
+      const int C = nv / kc;
       const uint32_t off_sym = kHdr + (uint32_t)pad_to(2 * lmax, 4);
       const uint32_t off_chunk = off_sym + (uint32_t)pad_to(2 * D, 4);
       const uint32_t off_pay = off_chunk + (uint32_t)pad_to(2 * C, 4);
@@ -373,7 +381,7 @@ struct Worker {
         }
       }
       __syncthreads();
-      if (!bad && tid < C && !m->err) decode_chunk(qb + tid * kChunk, (const uint32_t*)(sm + off_pay), nwords,
+      if (!bad && tid < C && !m->err) decode_chunk(qb + tid * kc, (const uint32_t*)(sm + off_pay), nwords,
                                                    cstart[tid], cstart[tid + 1], lut, symtab, D, lmax);
     }
     if (bad && tid == 0) atomicOr(&m->err, kStCorrupt);
@@ -466,7 +474,7 @@ struct Worker {
     wi += 2;
     bool cerr = false;
 #pragma unroll 4
-    for (int i = 0; i < kChunk; ++i) {
+    for (int i = 0; i < kc; ++i) {
       if (nbuf < 32) {
         buf |= (uint64_t)(wi < nwords ? w[wi] : 0u) << (32 - nbuf);
         ++wi;
@@ -870,7 +878,7 @@ __device__ void Worker<Real>::encode(int g, unsigned long long blk, const PassAr
   // complex128 with more verbatim values than the lists hold: the section goes straight to
   // the output like complex64's; the raw values come from a second transform (pass_group)
   const bool big = !kMask && nverb > kVmax;
-  const int C = nv / kChunk;
+  const int C = nv / kc;
   // ---- pass 1: statistics and the symbol histogram over this thread's values ----
   // (hash table; runs of equal symbols merged before an insert; inserts stop once the block
   // has more distinct symbols than Huffman mode takes)
@@ -1106,7 +1114,7 @@ __device__ void Worker<Real>::encode(int g, unsigned long long blk, const PassAr
         // chunk c covers threads [c*64/vpt, (c+1)*64/vpt)
         // chunk c covers threads [c*tpc, (c+1)*tpc); the thread starts go to the (now free)
         // internal-weight array
-        const int tpc = kChunk / vpt;
+        const int tpc = kc / vpt;
         uint32_t* tstart = wint;
         tstart[tid] = start;
         if (tid == 0) tstart[T] = tot;

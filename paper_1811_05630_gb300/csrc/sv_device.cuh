@@ -23,7 +23,9 @@ namespace sv {
 // ---- format constants -----------------------------------------------------------------
 constexpr int kHdr = 16;
 constexpr int kRadius = 32767;
-constexpr int kChunk = 32;            // symbols per decode chunk
+// Huffman symbols per stored chunk bit count (one decoding thread per chunk): a format
+// parameter of the state, 16, 32 or 64
+constexpr int kChunkDefault = 32, kChunkMin = 16;
 constexpr int kHuffMaxD = 256;        // more distinct symbols: PACK
 constexpr int kHashSlots = 512;       // >= 2 * kHuffMaxD
 constexpr int kLutBits = 10;          // decode table width

@@ -14,7 +14,7 @@ cudaError_t launch_pass_compact(const PassArgs& a, int dtype, cudaStream_t st);
 // The fused pass over the block-groups of many states (one descriptor each).
 cudaError_t launch_pass_batch(const PassArgs* descs, const unsigned long long* gprefix, int nstates,
                               unsigned long long total_groups, int b, int Gmax, int Kmax, int dtype,
-                              int threads, cudaStream_t st);
+                              int threads, int chunk, cudaStream_t st);
 // Norm finalization after a pass (one CTA per state): verbatim-sum tree when needed, N, sigma,
 // statistics; resets the bump of the arena the next pass writes.
 cudaError_t launch_norm(DevScalars* sc, const double* vsum, unsigned long long nb, double* tree, double two2,

@@ -116,6 +116,7 @@ __global__ void __launch_bounds__(256) k_pass_batch(const PassArgs* __restrict__
       __syncthreads();
       cur = lo;
       w.qp = as->qp;
+      w.kc = as->chunk ? as->chunk : kChunkDefault;
       sigma = as->use_sigma ? *(volatile double*)&as->sc->sigma : 1.0;
       if (w.m->live && sizeof(Real) == 8 && threadIdx.x == 0) fast_prepare(fg, *as, sigma);
     }
@@ -131,7 +132,7 @@ __global__ void __launch_bounds__(256) k_pass_batch(const PassArgs* __restrict__
 
 template <typename Real, int KM>
 static cudaError_t launch_pass_batch_k(const PassArgs* descs, const unsigned long long* gprefix, int nstates,
-                                       unsigned long long total_groups, int b, int Gmax, int threads,
+                                       unsigned long long total_groups, int b, int Gmax, int threads, int chunk,
                                        cudaStream_t st) {
   const Layout L = make_layout(b, Gmax, (int)sizeof(Real), true);  // the kernel's layout
   static bool configured = false;
@@ -142,6 +143,7 @@ static cudaError_t launch_pass_batch_k(const PassArgs* descs, const unsigned lon
   }
   if (L.total > 227 * 1024) return cudaErrorInvalidValue;
   const int T = threads_ok(b, threads) ? threads : worker_threads(b);
+  if (!chunk_ok(b, chunk, T)) return cudaErrorInvalidValue;
   unsigned long long grid = total_groups;
   if (grid > 0x7fffffffull) grid = 0x7fffffffull;
   if (grid == 0) return cudaSuccess;
@@ -151,16 +153,17 @@ static cudaError_t launch_pass_batch_k(const PassArgs* descs, const unsigned lon
 
 cudaError_t launch_pass_batch(const PassArgs* descs, const unsigned long long* gprefix, int nstates,
                               unsigned long long total_groups, int b, int Gmax, int Kmax, int dtype,
-                              int threads, cudaStream_t st) {
+                              int threads, int chunk, cudaStream_t st) {
   const unsigned long long tg = total_groups;
+  const int c = chunk ? chunk : kChunkDefault;
   if (dtype == 1) {
-    if (Kmax <= 2) return launch_pass_batch_k<float, 2>(descs, gprefix, nstates, tg, b, Gmax, threads, st);
-    if (Kmax <= 4) return launch_pass_batch_k<float, 4>(descs, gprefix, nstates, tg, b, Gmax, threads, st);
-    return launch_pass_batch_k<float, 8>(descs, gprefix, nstates, tg, b, Gmax, threads, st);
+    if (Kmax <= 2) return launch_pass_batch_k<float, 2>(descs, gprefix, nstates, tg, b, Gmax, threads, c, st);
+    if (Kmax <= 4) return launch_pass_batch_k<float, 4>(descs, gprefix, nstates, tg, b, Gmax, threads, c, st);
+    return launch_pass_batch_k<float, 8>(descs, gprefix, nstates, tg, b, Gmax, threads, c, st);
   }
-  if (Kmax <= 2) return launch_pass_batch_k<double, 2>(descs, gprefix, nstates, tg, b, Gmax, threads, st);
-  if (Kmax <= 4) return launch_pass_batch_k<double, 4>(descs, gprefix, nstates, tg, b, Gmax, threads, st);
-  return launch_pass_batch_k<double, 8>(descs, gprefix, nstates, tg, b, Gmax, threads, st);
+  if (Kmax <= 2) return launch_pass_batch_k<double, 2>(descs, gprefix, nstates, tg, b, Gmax, threads, c, st);
+  if (Kmax <= 4) return launch_pass_batch_k<double, 4>(descs, gprefix, nstates, tg, b, Gmax, threads, c, st);
+  return launch_pass_batch_k<double, 8>(descs, gprefix, nstates, tg, b, Gmax, threads, c, st);
 }
 
 cudaError_t launch_pass(const PassArgs& a, int dtype, cudaStream_t st) {

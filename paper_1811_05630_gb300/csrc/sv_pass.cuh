@@ -457,6 +457,7 @@ __device__ __forceinline__ void pass_body(const PassArgs& a) {
   const Layout L = make_layout(a.b, a.G, (int)sizeof(Real));
   Worker<Real> w;
   w.init(smem, L, a.b, a.qp);
+  if (a.chunk) w.kc = a.chunk;
   // A state poisoned by an earlier pass (or by another CTA of this one) is skipped. One
   // thread reads the flag so that the whole CTA takes the same branch.
   if (threadIdx.x == 0) {
@@ -502,6 +503,7 @@ static cudaError_t launch_pass_k(const PassArgs& a, cudaStream_t st) {
   }
   if (L.total > 227 * 1024) return cudaErrorInvalidValue;
   const int T = threads_ok(a.b, a.threads) ? a.threads : worker_threads(a.b);
+  if (!chunk_ok(a.b, a.chunk ? a.chunk : kChunkDefault, T)) return cudaErrorInvalidValue;
   unsigned long long grid = a.ngroups;
   if (grid > 0x7fffffffull) grid = 0x7fffffffull;
   if constexpr (COMPACT) k_pass_c<Real, KM><<<(unsigned int)grid, T, L.total, st>>>(a);

@@ -71,6 +71,7 @@ _SIGS = {
     "sv_sync": ([_vp], _i),
     "sv_set_threads": ([_vp, _i], _i),
     "sv_set_compact": ([_vp, _i], _i),
+    "sv_set_chunk": ([_vp, _i], _i),
     "sv_measure_probs": ([_vp, _vp, _i, _vp], _i),
     "sv_amplitudes": ([_vp, _vp, _sz, _vp], _i),
     "sv_read_amplitudes": ([_vp, _u64, _u64, _vp], _i),
@@ -176,6 +177,10 @@ class State:
     def set_threads(self, threads: int) -> None:
         """CTA size of the fused pass (0: default); results do not depend on it."""
         _check(_L.sv_set_threads(self._h, int(threads)), "sv_set_threads")
+
+    def set_chunk(self, chunk: int) -> None:
+        """Huffman chunk size of the block format (16, 32, 64); resets the state to |0...0>."""
+        _check(_L.sv_set_chunk(self._h, int(chunk)), "sv_set_chunk")
 
     def set_compact(self, on: bool) -> None:
         """Register-capped build of the fused pass for 1- and 2-qubit gates (results unchanged)."""

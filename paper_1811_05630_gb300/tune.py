@@ -1,5 +1,5 @@
-"""Autotuner for the block size (block_log2), the CTA size and the register budget of the
-fused pass.
+"""Autotuner for the block size (block_log2), the CTA size, the register budget of the
+fused pass and the Huffman chunk size of the block format.
 
 The block size sets the codec's parallel unit: small blocks give more CTAs per pass and
 more CTAs per SM (less shared memory each), large blocks amortize the per-block codebook
@@ -55,13 +55,16 @@ def thread_candidates(b: int) -> List[int]:
 
 
 def probe(pool: sv.Pool, n: int, dtype: int, eb: float, b: int, prefix: Sequence[Gate], timed: Sequence[Gate],
-          basis: int = 0, threads: int = 0, compact: bool = False) -> float:
+          basis: int = 0, threads: int = 0, compact: bool = False, chunk: int = 32) -> float:
     """Fused-kernel milliseconds per pass for `timed` after `prefix`, at block size b, CTA
-    size `threads` (0: the default) and with or without the register-capped build."""
+    size `threads` (0: the default), with or without the register-capped build, and Huffman
+    chunk size `chunk`."""
     st = sv.State(pool, n, n, eb, dtype, block_log2=b)
     try:
         st.set_threads(threads)
         st.set_compact(compact)
+        if chunk != 32:
+            st.set_chunk(chunk)
         st.reset_basis(basis)
         st.run(prefix)
         st.sync()
@@ -75,12 +78,14 @@ def probe(pool: sv.Pool, n: int, dtype: int, eb: float, b: int, prefix: Sequence
 
 def best_config(n: int, dtype: int, eb: float, kind: str, prefix: Sequence[Gate], timed: Sequence[Gate],
                 basis: int = 0, candidates: Iterable[int] = (8, 9, 10, 11, 12), pool: Optional[sv.Pool] = None,
-                use_cache: bool = True) -> dict:
-    """Tune (block_log2, threads, register-capped build) for a workload; returns
-    {"block_log2": b, "threads": T, "compact": c, "ms_per_pass": {"b/T/c": ms}}."""
+                use_cache: bool = True, chunks: Iterable[int] = (32,)) -> dict:
+    """Tune (block_log2, threads, register-capped build, Huffman chunk size) for a workload;
+    returns {"block_log2": b, "threads": T, "compact": c, "chunk": k, "ms_per_pass":
+    {"b/T/c/k": ms}}. The chunk size also changes the compressed size (16 more bits per
+    chunk), so `chunks` limits the sizes tried (the default: 32 only, the format default)."""
     key = _key(n, dtype, eb, kind)
     cache = _load() if use_cache else {}
-    if key in cache and "compact" in cache[key]:
+    if key in cache and "chunk" in cache[key]:
         return cache[key]
     own = pool is None
     if own:
@@ -92,13 +97,17 @@ def best_config(n: int, dtype: int, eb: float, kind: str, prefix: Sequence[Gate]
                 continue
             for t in thread_candidates(b):
                 for c in ((0, 1) if t >= 128 else (0,)):
-                    times[(b, t, c)] = probe(pool, n, dtype, eb, b, prefix, timed, basis, threads=t, compact=bool(c))
+                    for k in chunks:
+                        if (2 << b) // k > t:
+                            continue
+                        times[(b, t, c, k)] = probe(pool, n, dtype, eb, b, prefix, timed, basis, threads=t,
+                                                    compact=bool(c), chunk=k)
     finally:
         if own:
             pool.close()
     best = min(times, key=times.get)
-    res = {"block_log2": best[0], "threads": best[1], "compact": bool(best[2]),
-           "ms_per_pass": {"%d/%d/%d" % k: v for k, v in sorted(times.items())}}
+    res = {"block_log2": best[0], "threads": best[1], "compact": bool(best[2]), "chunk": best[3],
+           "ms_per_pass": {"%d/%d/%d/%d" % k: v for k, v in sorted(times.items())}}
     if use_cache:
         cache[key] = res
         _store(cache)

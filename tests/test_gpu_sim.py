@@ -153,7 +153,7 @@ def _gate(m, targets, controls=(), name=""):
     return C.Gate(np.asarray(m, dtype=np.complex128), tuple(targets), tuple(controls), name)
 
 
-def run_compare_reuse(sv, pool, n, b, dtype, eb, x, gates, threads=0, compact=False):
+def run_compare_reuse(sv, pool, n, b, dtype, eb, x, gates, threads=0, compact=False, chunk=32):
     """run_compare, gate by gate, summing the blocks each pass re-emitted unchanged."""
     st = sv.State(pool, n, n, eb, dtype, block_log2=b)
     reused = 0
@@ -161,8 +161,10 @@ def run_compare_reuse(sv, pool, n, b, dtype, eb, x, gates, threads=0, compact=Fa
         if threads:
             st.set_threads(threads)
         st.set_compact(compact)
+        if chunk != 32:
+            st.set_chunk(chunk)
         st.reset_basis(x)
-        cs = oracle.CompressedSim(n, n, b, dtype, eb, x)
+        cs = oracle.CompressedSim(n, n, b, dtype, eb, x, chunk=chunk)
         for i, g in enumerate(gates):
             st.apply(g.matrix, g.targets, g.controls)
             cs.apply(g.matrix, g.targets, g.controls)
@@ -237,6 +239,28 @@ def test_launch_shape_does_not_change_results(sv, pool, threads, compact, dtype)
     n, b = 12, 10
     gates = C.qft(n)[:20] + C.random_brickwork(n, 1, seed=8)
     run_compare_reuse(sv, pool, n, b, dtype, 1e-7, C.seeded_index(6, n), gates, threads=threads, compact=compact)
+
+
+@pytest.mark.parametrize("chunk,b,threads", [(16, 10, 128), (16, 9, 64), (64, 10, 64), (64, 6, 32)])
+@pytest.mark.parametrize("dtype", [oracle.C128, oracle.C64])
+def test_huffman_chunk_size_bit_exact(sv, pool, chunk, b, threads, dtype):
+    # the chunk size changes the stream bytes (its chunk table) but not the decoded values;
+    # every pass must equal the oracle run with the same chunk size
+    n = 12
+    gates = C.qft(n)[:30] + C.random_brickwork(n, 1, seed=3)
+    run_compare_reuse(sv, pool, n, b, dtype, 1e-6, C.seeded_index(8, n), gates, threads=threads, chunk=chunk)
+
+
+def test_huffman_chunk_size_checked(sv, pool):
+    st = sv.State(pool, 14, 14, 1e-6, oracle.C128, block_log2=12)  # default CTA: 256 threads
+    try:
+        for bad in (8, 24, 128, 16):  # 16: 8192 / 16 = 512 chunks > 256 threads
+            with pytest.raises(sv.SvError):
+                st.set_chunk(bad)
+        st.set_chunk(64)
+        st.set_chunk(32)
+    finally:
+        st.close()
 
 
 def test_cta_size_checked(sv, pool):
