@@ -27,6 +27,8 @@
  *   - Streams: every call is ordered on the state's CUDA stream (cudaStream_t passed as
  *     void*, NULL = legacy default stream). Calls that return host data synchronize that
  *     stream; the others are asynchronous.
+ *   - Host threads: a state or a batch is used by one host thread at a time; states on one
+ *     pool may be used from different threads (the pool's allocator is locked).
  *   - Errors: every call returns 0 (SV_OK) or a negative SV_ERR_* code. An error raised
  *     inside a kernel (stream corruption, arena overflow, norm collapse) is recorded on the
  *     device and returned by the next synchronizing call; later passes of that state are

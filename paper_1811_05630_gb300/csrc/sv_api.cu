@@ -301,6 +301,7 @@ void build_args(const sv_state* s, const Logged& lg, PassArgs& a) {
 
 // Launch pass + norm tree + finalize for one logged step of one state.
 int launch_logged(sv_state* s, const Logged& lg) {
+  if (!s->arena[lg.in_id] || !s->arena[lg.out_id]) return SV_ERR_OOM;  // lost to a failed regrowth
   PassArgs a;
   build_args(s, lg, a);
   std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
@@ -364,8 +365,11 @@ int reserve_arena(sv_state* s, int id, size_t want) {
   if (s->arena_r[id].bytes >= want) return SV_OK;
   const size_t old = s->arena_r[id].bytes;
   region_free(s->pool, &s->arena_r[id]);
-  if (!region_alloc(s->pool, &s->arena_r[id], want) && !region_alloc(s->pool, &s->arena_r[id], old))
+  if (!region_alloc(s->pool, &s->arena_r[id], want) && !region_alloc(s->pool, &s->arena_r[id], old)) {
+    s->arena[id] = nullptr;  // no arena: the state takes no more passes
+    s->sticky_err = SV_ERR_OOM;
     return SV_ERR_OOM;
+  }
   s->arena[id] = pool_ptr(s->pool, s->arena_r[id].off);
   return SV_OK;
 }
@@ -375,8 +379,10 @@ int grow_arena(sv_state* s, int id, size_t need) {
   // further, and every overflow costs a replay
   size_t want = std::max(s->arena_r[id].bytes + s->arena_r[id].bytes / 2, 2 * need);
   region_free(s->pool, &s->arena_r[id]);
-  if (!region_alloc(s->pool, &s->arena_r[id], want)) {
-    if (!region_alloc(s->pool, &s->arena_r[id], need)) return SV_ERR_OOM;
+  if (!region_alloc(s->pool, &s->arena_r[id], want) && !region_alloc(s->pool, &s->arena_r[id], need)) {
+    s->arena[id] = nullptr;  // no arena: the state takes no more passes
+    s->sticky_err = SV_ERR_OOM;
+    return SV_ERR_OOM;
   }
   s->arena[id] = pool_ptr(s->pool, s->arena_r[id].off);
   return SV_OK;
@@ -1004,6 +1010,7 @@ int sv_batch_apply(sv_batch* bt, sv_state* const* states, const sv_gate_t* gates
     int nh = 0;
     for (int l = 0; l < g.k; ++l) nh += g.targets[l] >= s->b;
     if (nh > 2) return SV_ERR_UNSUPPORTED;
+    if (!s->arena[0] || !s->arena[1]) return SV_ERR_OOM;  // lost to a failed regrowth
   }
   // stage descriptors and tables in the next pinned buffer of the ring
   const int slot = bt->ring;
