@@ -50,7 +50,7 @@ extern "C" {
 #define SV_ERR_CUDA (-3)        /* a CUDA runtime call failed */
 #define SV_ERR_NORM (-4)        /* stored norm is zero or not finite */
 #define SV_ERR_CORRUPT (-5)     /* a block stream failed the decoder's bounds checks */
-#define SV_ERR_UNSUPPORTED (-6) /* outside this build's limits (see each call) */
+#define SV_ERR_UNSUPPORTED (-6) /* outside the library's limits (see each call) */
 #define SV_ERR_TIMEOUT (-7)     /* a bounded device wait ran out */
 #define SV_ERR_INTERNAL (-8)    /* a device-side consistency check failed (a library bug) */
 
@@ -115,7 +115,7 @@ int sv_reset_basis(sv_state* s, uint64_t index);
  * Normalize(S) (global scale 1/sqrt(N) of the stored norm N), GateComputation(G, S),
  * Compress(S). Slices are processed in every pass, also where the controls make the gate
  * the identity. Targets at or above block_log2 pair the 2^h coupled blocks inside one CTA
- * (h <= 2 in this build: SV_ERR_UNSUPPORTED otherwise). k in 1..3 targets.
+ * (h <= 2: SV_ERR_UNSUPPORTED otherwise). k in 1..3 targets.
  * Plain path: G applied in place to the uncompressed vector (no normalization).
  * Asynchronous; errors raised on the device are reported by the next synchronizing call.
  * ------------------------------------------------------------------------------------- */
