@@ -111,17 +111,21 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# the device-code sources of the fused pass (host-side files do not change what it moves)
+KERNEL_SOURCES = ("sv_block.cuh", "sv_device.cuh", "sv_pass.cuh", "sv_pass_compact.cu", "sv_kernels.cu")
+
+
 def source_digest() -> str:
-    """Digest of the kernel sources, to tie an ncu traffic figure to the code it measured."""
+    """Digest of the fused pass's device sources, to tie an ncu traffic figure to the code it
+    measured."""
     import hashlib
 
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1811_05630_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(f.encode())
-            with open(os.path.join(d, f), "rb") as fh:
-                h.update(fh.read())
+    for f in KERNEL_SOURCES:
+        h.update(f.encode())
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 

@@ -133,6 +133,8 @@ struct sv_state {
   int threads = 0;                  // CTA size of the fused pass (0: default)
   bool compact = false;             // register-capped build of the pass (1- and 2-qubit gates)
   int huff_chunk = 32;              // Huffman chunk size of the block format
+  DevScalars* hsc = nullptr;        // pinned host copy of the device scalars
+  bool hsc_valid = false;           // hsc holds the state after every submitted pass
   // passes between status checks (an overflow poisons every later pass until the check
   // replays them): about 2 ms of device work, 1 after an overflow
   int sync_every = 16;
@@ -335,6 +337,7 @@ int log_step(sv_state* s, Logged&& lg) {
   if (s->sticky_err) return SV_OK;
   s->log.push_back(std::move(lg));
   s->since_check++;
+  s->hsc_valid = false;
   if (s->log.size() >= (size_t)s->sync_every) {
     const int rc = sv_sync(s);
     if (rc == SV_ERR_CUDA) return rc;
@@ -354,9 +357,21 @@ int submit(sv_state* s, Logged lg) {
 }
 
 int read_scalars(sv_state* s, DevScalars* h) {
-  cudaError_t e = cudaMemcpyAsync(h, s->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, s->st);
+  DevScalars* dst = s->hsc ? s->hsc : h;  // pinned when available: one short transfer
+  cudaError_t e = cudaMemcpyAsync(dst, s->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, s->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+  if (e == cudaSuccess && dst != h) *h = *dst;
   return cuda_err(e);
+}
+
+// The device scalars after every submitted pass: the copy the last clean sv_sync read, else a
+// fresh read (callers have synchronized).
+int current_scalars(sv_state* s, DevScalars* h) {
+  if (s->hsc && s->hsc_valid) {
+    *h = *s->hsc;
+    return SV_OK;
+  }
+  return read_scalars(s, h);
 }
 
 // Give arena `id` (not the live one) at least `want` bytes when the pool has room; keeps
@@ -516,6 +531,10 @@ int sv_create_ex(sv_pool* pool, int n, int sl, int bl, double eb, int dtype, siz
   }
   uint8_t* m = pool_ptr(pool, s->meta_r.off);
   s->sc = (DevScalars*)(m + o_sc);
+  if (cudaHostAlloc((void**)&s->hsc, sizeof(DevScalars), cudaHostAllocDefault) != cudaSuccess) {
+    cudaGetLastError();  // pageable transfers instead
+    s->hsc = nullptr;
+  }
   s->toff[0] = (unsigned long long*)(m + o_off0);
   s->toff[1] = (unsigned long long*)(m + o_off1);
   s->tlen[0] = (unsigned int*)(m + o_len0);
@@ -531,6 +550,7 @@ int sv_create_ex(sv_pool* pool, int n, int sl, int bl, double eb, int dtype, siz
     if (!region_alloc(pool, &s->arena_r[id], init_cap)) {
       region_free(pool, &s->arena_r[0]);
       region_free(pool, &s->meta_r);
+      if (s->hsc) cudaFreeHost(s->hsc);
       delete s;
       return SV_ERR_OOM;
     }
@@ -556,6 +576,7 @@ int sv_destroy(sv_state* s) {
     cudaEventDestroy(ev.first);
     cudaEventDestroy(ev.second);
   }
+  if (s->hsc) cudaFreeHost(s->hsc);
   region_free(s->pool, &s->psi_r);
   region_free(s->pool, &s->meta_r);
   region_free(s->pool, &s->arena_r[0]);
@@ -612,6 +633,7 @@ int sv_sync(sv_state* s) {
     if (rc) return rc;
     if (h.status == 0) {
       s->log.clear();
+      s->hsc_valid = s->hsc != nullptr;
       // an overflow costs a replay of every pass since the failed one: check about every
       // 2 ms of device work (the passes since the last check, over the time they took), at
       // most 256 passes apart
@@ -691,7 +713,7 @@ int sv_norm(sv_state* s, double* out) {
     return SV_OK;
   }
   DevScalars h;
-  rc = read_scalars(s, &h);
+  rc = current_scalars(s, &h);
   if (rc) return rc;
   *out = h.norm;
   return SV_OK;
@@ -729,7 +751,7 @@ int sv_stats(sv_state* s, sv_stats_t* out) {
     return SV_OK;
   }
   DevScalars h;
-  rc = read_scalars(s, &h);
+  rc = current_scalars(s, &h);
   if (rc) return rc;
   out->pass_index = h.pass_index;
   out->compressed_bytes = h.last_bytes;
