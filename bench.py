@@ -28,6 +28,7 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 from paper_1811_05630_gb300 import circuits as C  # noqa: E402
+from paper_1811_05630_gb300 import report  # noqa: E402
 
 METRIC = "amplitude-updates/s compressed vs plain at fidelity>=1-1e-6; ratio; p99 latency"
 UNIT = "amp-updates/s"
@@ -414,7 +415,7 @@ def run_ours(args, rank, world, dist):
                        "l2": "flushed between timed steps (512 MiB write, untimed); compressed state %d B"
                              % stats["compressed_bytes"],
                        "compressed_bytes": stats["compressed_bytes"],
-                       "compression_ratio": (16 << n) / max(1, stats["compressed_bytes"]),
+                       "compression_ratio": report.compression_ratio(n, wl["dtype"], max(1, stats["compressed_bytes"])),
                        "plain_amp_updates_per_s": plain,
                        "ratio_plain_over_compressed": (plain / (value / world)) if isinstance(plain, float) else None,
                        "fidelity": fid},
@@ -467,7 +468,7 @@ def run_full_circuit(args):
         st.set_chunk(args.chunk)
     st.reset_basis(wl["basis"])
     st.sync()
-    raw = (16 if wl["dtype"] == 2 else 8) << n
+    raw = report.raw_state_bytes(n, wl["dtype"])
     per_gate = []
     reused = 0
     stream = torch.cuda.current_stream()
@@ -508,6 +509,8 @@ def run_full_circuit(args):
         "kernel_ms_total": kern_ms, "wall_s": wall, "fused_kernel_gbs": alg_bytes / (kern_ms * 1e-3) / 1e9,
         "fidelity_vs_closed_form": fid,
         "compression_ratio_final": raw / per_gate[-1], "compression_ratio_min": raw / max(per_gate),
+        "memory_fraction_max": report.memory_fraction(raw / max(per_gate)),
+        "extra_qubits_at_min_ratio": report.extra_qubits(raw / max(per_gate)),
         "compressed_bytes_max": max(per_gate), "compressed_bytes_final": per_gate[-1],
         "marginal_probs_max_abs_dev_from_uniform": float(np.abs(p - 2.0 ** -m).max()),
         "sampled_prob_ratio_mean": float(samp.mean()), "sampled_prob_ratio_std": float(samp.std()),
