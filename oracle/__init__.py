@@ -14,9 +14,11 @@ Compression" (PMES 2018).
   * ``huffman_lengths`` — the two-queue Huffman code lengths the codec uses.
 
 Parity pins (tests/test_oracle_*.py) check every function here against closed forms,
-invariants, brute force and an independent textbook Huffman; the end-to-end O2 result has
-no value printed in the paper to pin it exactly and is pinned by exactness on
-grid-preserving circuits and a fidelity bound against O1.
+invariants, brute force and an independent textbook Huffman. The paper prints no value of
+O2's output; a single O2 pass is pinned element by element against the normalized gate
+(G x' / sqrt(N), by an independent tensor contraction) within eb, exactly on power-of-two
+norms, and whole circuits by exactness on grid-preserving circuits, grouping invariance and
+a fidelity bound against O1.
 """
 from __future__ import annotations
 

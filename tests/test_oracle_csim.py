@@ -18,6 +18,7 @@ import pytest
 
 import oracle
 from paper_1811_05630_gb300 import circuits as C
+from test_oracle_plain import apply_by_tensordot, random_unitary
 
 
 def fidelity(a, b):
@@ -126,3 +127,72 @@ def test_complex64_variant_close_to_fp64():
     ps = oracle.PlainSim(n, oracle.C128, x).run(gates).state
     assert 1 - fidelity(c64, ps) < 1e-6
     assert 1 - fidelity(c128, ps) < 1e-6
+
+
+@pytest.mark.parametrize("scale,sigma", [(2.0, 0.5), (0.5, 2.0)])
+def test_normalize_rescales_by_inverse_sqrt_of_stored_norm(scale, sigma):
+    # Alg. 1 Normalize: y = x' / sqrt(N) with N the stored norm. On the grid of eb = 2^-11
+    # (multiples of 2^-10), 256 amplitudes of +-scale/16 store N = scale^2 exactly; sigma is
+    # then a power of two and the pass after an X gate is exact: every value scales by sigma.
+    n, eb = 10, 2.0 ** -11
+    rng = np.random.default_rng(5)
+    v = np.zeros(1 << n, dtype=np.complex128)
+    idx = rng.choice(1 << n, 256, replace=False)
+    signs = rng.choice([-1.0, 1.0], 256)
+    v[idx] = np.where(rng.random(256) < 0.5, signs, 1j * signs) * scale / 16
+    cs = oracle.CompressedSim(n, 7, 5, oracle.C128, eb)
+    cs.load(v)
+    assert cs.norm == scale * scale
+    for t in (2, 8):  # a target inside a slice, then one above the slice
+        cs.apply(C.X, (t,))
+        v = apply_by_tensordot(v, n, C.X, (t,), ())
+        assert np.array_equal(cs.read(), v * sigma)
+        assert cs.norm == 1.0
+        v = v * sigma
+        sigma = 1.0
+
+
+SINGLE_PASS_GATES = [
+    ("1q low target", 1, (2,), ()),
+    ("1q target above the slice", 1, (7,), ()),
+    ("2q across slices", 2, (1, 8), ()),
+    ("controlled, control above the slice", 1, (3,), (8,)),
+    ("two controls", 1, (0,), (4, 6)),
+    ("3q", 3, (5, 0, 7), ()),
+]
+
+
+@pytest.mark.parametrize("dtype", [oracle.C128, oracle.C64])
+@pytest.mark.parametrize("case", SINGLE_PASS_GATES, ids=[c[0] for c in SINGLE_PASS_GATES])
+def test_single_pass_is_normalized_gate_within_bound(dtype, case):
+    # One pass of Alg. 1 on a state whose stored norm N is not 1: every amplitude after the
+    # pass lies within eb (per component) of (G y)_i, y = x' / sqrt(N), x' the decompressed
+    # values before the pass, computed here by an independent tensor contraction; amplitudes
+    # the gate leaves alone (controls unset) are rescaled too, since every slice goes through
+    # the cycle. The new stored norm is the squared norm of the stored values.
+    _, k, targets, controls = case
+    n, sl, b = 9, 6, 5
+    eb = 1e-6 if dtype == oracle.C128 else 1e-4
+    rng = np.random.default_rng(40 + k + len(controls))
+    v = rng.standard_normal(1 << n) + 1j * rng.standard_normal(1 << n)
+    v *= 1.7 / np.linalg.norm(v)
+    G = random_unitary(rng, 1 << k)
+    cs = oracle.CompressedSim(n, sl, b, dtype, eb)
+    cs.load(v)
+    x = cs.read().astype(np.complex128)
+    N = cs.norm
+    # N is the norm of the stored grid values q 2eb; complex64 decodes them rounded to float
+    rel = 1e-12 if dtype == oracle.C128 else 2.0 ** -22
+    assert abs(N - np.vdot(x, x).real) <= rel * N
+    assert abs(N - 1.7 ** 2) < 1e-3
+    cs.apply(G, targets, controls)
+    y = apply_by_tensordot(x / math.sqrt(N), n, G, targets, controls)
+    got = cs.read().astype(np.complex128)
+    # FP arithmetic of the pass (FP64, or FP32 for complex64) on top of the quantization bound
+    fp = (1e-15 if dtype == oracle.C128 else 6e-7) * (2 ** k) * np.abs(x).max() / math.sqrt(N)
+    assert np.abs(got.real - y.real).max() <= eb + fp
+    assert np.abs(got.imag - y.imag).max() <= eb + fp
+    assert abs(cs.norm - np.vdot(got, got).real) <= rel * cs.norm
+    # the bound is tight enough to see a wrong scale: 1/N instead of 1/sqrt(N) misses by far more
+    wrong = apply_by_tensordot(x / N, n, G, targets, controls)
+    assert np.abs(got - wrong).max() > 100 * eb
