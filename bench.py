@@ -130,21 +130,28 @@ def source_digest() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(workload: str):
+def recorded_traffic(workload: str, block_log2: int, threads: int, compact: bool):
     """DRAM bytes per fused-pass launch from the committed ncu summary of this workload, when
-    it was taken on these exact kernel sources: (bytes, description of the captured launches),
-    else (None, None)."""
+    it was taken on these exact kernel sources and this launch configuration (block size, CTA
+    size, build): (bytes, description of the captured launches), else (None, why not)."""
     path = os.path.join(ROOT, "profiles", "k_pass_%s.md" % workload)
+    why = "no ncu capture recorded for this workload"
     try:
         with open(path) as f:
             for line in f:
                 if line.startswith("TRAFFIC "):
                     kv = dict(x.split("=", 1) for x in line.split()[1:])
-                    if kv.get("digest") == source_digest():
-                        return float(kv["bytes_per_launch"]), kv.get("launches", "").replace("_", " ")
+                    if kv.get("digest") != source_digest():
+                        why = "kernel sources changed since the ncu capture"
+                        continue
+                    if (int(kv["block_log2"]), int(kv["threads"]), bool(int(kv["compact"]))) != (
+                            block_log2, threads, bool(compact)):
+                        why = "no ncu capture at this launch configuration"
+                        continue
+                    return float(kv["bytes_per_launch"]), kv.get("launches", "").replace("_", " ")
     except (OSError, ValueError, KeyError):
         pass
-    return None, None
+    return None, why
 
 
 def peaks():
@@ -361,11 +368,15 @@ def run_ours(args, rank, world, dist):
         pk = peaks()
         kern_s = kern_ms * 1e-3
         achieved = alg_bytes / kern_s / 1e9 if kern_s > 0 else 0.0
-        traffic, traffic_src = recorded_traffic(wl["name"])
+        # the default CTA size is one thread per 32-value decode chunk, 32 to 256 threads
+        eff_threads = int(wl.get("threads") or min(256, max(32, (2 << wl["block_log2"]) // 32)))
+        traffic, traffic_src = recorded_traffic(wl["name"], wl["block_log2"], eff_threads,
+                                                bool(wl.get("compact")))
         roof = {"bound": "hbm", "achieved": achieved, "peak": pk.get("hbm_gbs"), "unit": "GB/s",
                 "frac": achieved / pk.get("hbm_gbs", 1.0), "traffic": traffic,
                 "traffic_source": traffic_src, "source_digest": source_digest(),
-                "kernel": "k_pass<double>", "kernel_ms_per_launch": kern_ms / max(npass, 1),
+                "kernel": "k_pass_c (fused pass, register-capped build)" if wl.get("compact")
+                else "k_pass (fused pass)", "kernel_ms_per_launch": kern_ms / max(npass, 1),
                 "alg_bytes_per_launch": alg_bytes / max(npass, 1),
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "fallback" not in pk else "fallback"}
         # plain GPU path on the same gates, where it fits
