@@ -386,29 +386,52 @@ struct Worker {
     }
     if (bad && tid == 0) atomicOr(&m->err, kStCorrupt);
     __syncthreads();
-    // inverse Lorenzo: q_j = q_{j-2} + delta_j, one running sum per plane (each thread sums
-    // its run held in registers, a block scan gives the run's offsets, then it writes the codes)
+    // inverse Lorenzo: q_j = q_{j-2} + delta_j, one running sum per plane: each thread sums
+    // its run, a block scan gives the run's offsets, then it reads the run again and writes the
+    // codes (no run held in registers across the scan). Runs of 4 or more values move as
+    // 16-byte words: a thread's run starts vpt words after its neighbour's, and word-wide
+    // accesses at that stride would share banks vpt/2 ways.
+    int32_t* run = qb + tid * vpt;
+    const bool wide = (vpt & 3) == 0;
     int2 loc = make_int2(0, 0);
-    int32_t dv[32];
-#pragma unroll
-    for (int i = 0; i < 32; ++i)
-      if (i < vpt) {
-        dv[i] = qb[tid * vpt + i];
-        if (i & 1) loc.y += dv[i];
-        else loc.x += dv[i];
+    if (wide) {
+      for (int i = 0; i < vpt; i += 4) {
+        const int4 v = *(const int4*)(run + i);
+        loc.x += v.x;
+        loc.y += v.y;
+        loc.x += v.z;
+        loc.y += v.w;
       }
-    int2 off = block_excl_scan_i2(loc, (int2*)m->red);
-#pragma unroll
-    for (int i = 0; i < 32; ++i)
-      if (i < vpt) {
-        if (i & 1) {
-          off.y += dv[i];
-          qb[tid * vpt + i] = off.y;
-        } else {
-          off.x += dv[i];
-          qb[tid * vpt + i] = off.x;
-        }
+    } else {
+      for (int i = 0; i < vpt; i += 2) {
+        const int2 v = *(const int2*)(run + i);
+        loc.x += v.x;
+        loc.y += v.y;
       }
+    }
+    int2 off = block_excl_scan_i2(loc, (int2*)m->red);  // syncs: every run is summed
+    if (wide) {
+      for (int i = 0; i < vpt; i += 4) {
+        const int4 v = *(const int4*)(run + i);
+        int4 o;
+        off.x += v.x;
+        o.x = off.x;
+        off.y += v.y;
+        o.y = off.y;
+        off.x += v.z;
+        o.z = off.x;
+        off.y += v.w;
+        o.w = off.y;
+        *(int4*)(run + i) = o;
+      }
+    } else {
+      for (int i = 0; i < vpt; i += 2) {
+        const int2 v = *(const int2*)(run + i);
+        off.x += v.x;
+        off.y += v.y;
+        *(int2*)(run + i) = make_int2(off.x, off.y);
+      }
+    }
     // verbatim section: ascending positions, then raw values (aligned to the value size)
     if (nverb > nv) {
       if (tid == 0) atomicOr(&m->err, kStCorrupt);
@@ -461,8 +484,10 @@ struct Worker {
     }
   }
 
-  // One 32-symbol chunk of a Huffman payload (shared-memory words), through a 64-bit bit
-  // buffer that holds at least 32 unread bits before every symbol.
+  // One K-symbol chunk of a Huffman payload (shared-memory words), through a 64-bit bit
+  // buffer that holds at least 32 unread bits before every symbol. The deltas leave in
+  // 16-byte words of four (chunks start K words apart, so word-wide stores of all threads
+  // would share one bank).
   __device__ __forceinline__ void decode_chunk(int32_t* out, const uint32_t* w, uint32_t nwords,
                                                uint32_t pos, uint32_t end, const uint32_t* lut,
                                                const uint16_t* symtab, int D, int lmax) {
@@ -473,51 +498,56 @@ struct Worker {
     int nbuf = 64 - sh;
     wi += 2;
     bool cerr = false;
-#pragma unroll 4
-    for (int i = 0; i < kc; ++i) {
-      if (nbuf < 32) {
-        buf |= (uint64_t)(wi < nwords ? w[wi] : 0u) << (32 - nbuf);
-        ++wi;
-        nbuf += 32;
-      }
-      const uint32_t pk = (uint32_t)(buf >> 32);
-      const uint32_t e = lut[pk >> (32 - kLutBits)];
-      int idx = -1, l = 0;
-      if (e) {
-        idx = (int)(e >> 8) - 1;
-        l = (int)(e & 0xff);
-      } else {
-        for (l = kLutBits + 1; l <= lmax; ++l) {
-          const int c = (int)(pk >> (32 - l));
-          if (m->lcount[l] && c >= m->first[l] && c - m->first[l] < m->lcount[l]) {
-            idx = m->offs[l] + c - m->first[l];
-            break;
-          }
-        }
-      }
-      if (idx < 0 || idx >= D) {
-        cerr = true;
-        break;
-      }
-      buf <<= l;
-      nbuf -= l;
-      pos += (uint32_t)l;
-      const int sym = symtab[idx];
-      int32_t d;
-      if (sym == 0) {
+    for (int i4 = 0; i4 < kc && !cerr; i4 += 4) {
+      int32_t r4[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
         if (nbuf < 32) {
           buf |= (uint64_t)(wi < nwords ? w[wi] : 0u) << (32 - nbuf);
           ++wi;
           nbuf += 32;
         }
-        d = (int32_t)(uint32_t)(buf >> 32);
-        buf <<= 32;
-        nbuf -= 32;
-        pos += 32;
-      } else {
-        d = sym - 32768;
+        const uint32_t pk = (uint32_t)(buf >> 32);
+        const uint32_t e = lut[pk >> (32 - kLutBits)];
+        int idx = -1, l = 0;
+        if (e) {
+          idx = (int)(e >> 8) - 1;
+          l = (int)(e & 0xff);
+        } else {
+          for (l = kLutBits + 1; l <= lmax; ++l) {
+            const int c = (int)(pk >> (32 - l));
+            if (m->lcount[l] && c >= m->first[l] && c - m->first[l] < m->lcount[l]) {
+              idx = m->offs[l] + c - m->first[l];
+              break;
+            }
+          }
+        }
+        if (idx < 0 || idx >= D) {
+          cerr = true;
+          r4[u] = 0;
+          continue;
+        }
+        buf <<= l;
+        nbuf -= l;
+        pos += (uint32_t)l;
+        const int sym = symtab[idx];
+        int32_t d;
+        if (sym == 0) {
+          if (nbuf < 32) {
+            buf |= (uint64_t)(wi < nwords ? w[wi] : 0u) << (32 - nbuf);
+            ++wi;
+            nbuf += 32;
+          }
+          d = (int32_t)(uint32_t)(buf >> 32);
+          buf <<= 32;
+          nbuf -= 32;
+          pos += 32;
+        } else {
+          d = sym - 32768;
+        }
+        r4[u] = d;
       }
-      out[i] = d;
+      *(int4*)(out + i4) = make_int4(r4[0], r4[1], r4[2], r4[3]);
     }
     if (cerr || pos != end) atomicOr(&m->err, kStCorrupt);
   }
@@ -899,16 +929,19 @@ __device__ void Worker<Real>::encode(int g, unsigned long long blk, const PassAr
   bs.nesc = 0;
   bs.cst = 1;
   {
-    int32_t pr = j0 >= 2 ? code(g, j0 - 2) : 0, pi = j0 >= 2 ? code(g, j0 - 1) : 0;
+    // Every quantity of this pass is independent of the order in which a thread visits its
+    // run, so thread t starts at offset (lane(t) * vpt / 32) of its run and wraps around: the
+    // 32 lanes of a warp then read 32 different banks at every step (runs start vpt words
+    // apart, and in-order visits would share banks vpt/2 ways). d_j = c_j - c_{j-2} reads both
+    // codes from shared memory.
+    const int rot = ((tid & 31) * vpt) >> 5;
     uint32_t run_sym = 0xFFFFFFFFu, run = 0;
-    for (int i = 0; i <= vpt; ++i) {
+    for (int k = 0; k <= vpt; ++k) {
       uint32_t sym = 0xFFFFFFFEu;
-      if (i < vpt) {
-        const int j = j0 + i;
+      if (k < vpt) {
+        const int j = j0 + ((k + rot) & (vpt - 1));
         const int32_t c = code(g, j);
-        const int32_t d = c - ((j & 1) ? pi : pr);
-        if (j & 1) pi = c;
-        else pr = c;
+        const int32_t d = c - (j >= 2 ? code(g, j - 2) : 0);
         const uint64_t s2 = (uint64_t)((int64_t)c * (int64_t)c);
         bs.sqh += s2 >> 32;
         bs.sql += s2 & 0xffffffffull;
