@@ -327,3 +327,32 @@ def test_traffic_record_needs_matching_sources_and_shape(monkeypatch, tmp_path):
     monkeypatch.setattr(bench, "source_digest", lambda: "def")
     assert bench.recorded_traffic("demo", 11, 256, True) == (None, "kernel sources changed since the ncu capture")
     assert bench.recorded_traffic("other", 11, 256, True)[0] is None
+
+
+def test_clock_summary_reads_throttle_reasons():
+    import bench
+
+    cs = bench.ClockSampler(0)
+    cs.rows = [
+        ["0", "2070", "2070", "812.3", "0x0000000000000000", "Not Active", "Not Active", "Not Active", "Not Active"],
+        ["0", "2055", "2070", "1390.1", "0x0000000000000004", "Not Active", "Not Active", "Not Active", "Active"],
+        ["0", "1980", "2070", "1402.0", "0x0000000000000008", "Active", "Not Active", "Not Active", "Active"],
+        ["0", "[N/A]", "2070"],  # a malformed line is skipped
+    ]
+    s = cs.summary()
+    assert s["samples"] == 3 and s["sm_mhz"] == 2055.0 and s["sm_max_mhz"] == 2070.0
+    assert s["reasons"] == ["hw_slowdown", "sw_power_cap"]
+    assert bench.ClockSampler(0).summary() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+
+
+def test_dense_stage_start():
+    import bench
+
+    # QFT: every gate of the stages of qubits n-1 .. block_log2 (H plus one controlled phase
+    # per lower qubit) comes before the first stage that mixes values inside a block
+    wl = {"name": "qft34", "n": 34, "block_log2": 11}
+    assert bench.start_of_dense_stage(wl) == sum(1 + j for j in range(33, 10, -1))
+    gates = C.qft(34)
+    i0 = bench.start_of_dense_stage(wl)
+    assert gates[i0].name == "H" and gates[i0].targets == (10,)
+    assert bench.start_of_dense_stage({"name": "grover20", "n": 20, "block_log2": 11}) == 20
