@@ -196,3 +196,33 @@ def test_single_pass_is_normalized_gate_within_bound(dtype, case):
     # the bound is tight enough to see a wrong scale: 1/N instead of 1/sqrt(N) misses by far more
     wrong = apply_by_tensordot(x / N, n, G, targets, controls)
     assert np.abs(got - wrong).max() > 100 * eb
+
+
+@pytest.mark.parametrize("dtype", [oracle.C128, oracle.C64])
+def test_stored_norm_counts_verbatim_values(dtype):
+    # Values with |x r| >= 2^29 are stored raw (verbatim). The stored norm N must still be the
+    # squared norm of every stored value, the raw ones included; and a pass over such a state
+    # rescales them like the rest.
+    n, sl, b = 8, 6, 5
+    eb = 1e-10 if dtype == oracle.C128 else 2e-8
+    lim = 2.0 ** 29 * 2 * eb  # the largest magnitude the quantizer takes
+    rng = np.random.default_rng(17)
+    v = (rng.standard_normal(1 << n) + 1j * rng.standard_normal(1 << n)) * lim / 8
+    big = rng.choice(1 << n, 12, replace=False)
+    v[big] = (3 + rng.random(12)) * lim * np.exp(2j * np.pi * rng.random(12))
+    cs = oracle.CompressedSim(n, sl, b, dtype, eb)
+    cs.load(v)
+    x = cs.read().astype(np.complex128)
+    rel = 1e-12 if dtype == oracle.C128 else 2.0 ** -22
+    if dtype == oracle.C128:
+        assert np.array_equal(x[big], v[big])  # raw values come back exactly
+    N = cs.norm
+    assert abs(N - np.vdot(x, x).real) <= rel * N
+    # the raw values carry most of the norm, so dropping them would miss by far more than rel
+    assert np.vdot(x[big], x[big]).real > 0.5 * N
+    cs.apply(C.X, (1,))
+    y = apply_by_tensordot(x / math.sqrt(N), n, C.X, (1,), ())
+    got = cs.read().astype(np.complex128)
+    fp = (1e-15 if dtype == oracle.C128 else 6e-7) * np.abs(y).max()
+    assert np.abs(got - y).max() <= math.sqrt(2) * eb + fp
+    assert abs(cs.norm - np.vdot(got, got).real) <= rel * cs.norm
