@@ -254,6 +254,7 @@ def test_chunk_table_matches_an_independent_decode(chunk, kind, eb):
     words = struct.unpack_from("<%dI" % ((p["pbits"] + 31) // 32), s, p["payload_off"])
     bits = "".join(format(w, "032b") for w in words)
     pos = 0
+    deltas = []
     for ci, stored in enumerate(p["chunks"]):
         start = pos
         for _ in range(chunk):
@@ -262,9 +263,24 @@ def test_chunk_table_matches_an_independent_decode(chunk, kind, eb):
                 L += 1
                 assert L <= 24
             sym = code_of[(int(bits[pos:pos + L], 2), L)]
-            pos += L + (32 if sym == 0 else 0)
+            pos += L
+            if sym == 0:  # escape: the 32-bit delta follows
+                d = int(bits[pos:pos + 32], 2)
+                deltas.append(d - (1 << 32) if d >= 1 << 31 else d)
+                pos += 32
+            else:
+                deltas.append(sym - 32768)
         assert pos - start == stored, ci
     assert pos == p["pbits"]
+    # the values from the decoded deltas by the format's own rule: Lorenzo per plane
+    # (q_j = q_{j-2} + delta_j over interleaved re/im, q_{-2} = q_{-1} = 0), x' = q * fl(2 eb)
+    assert p["nverb"] == 0 and len(deltas) == 2 << b
+    q = np.zeros(2 << b, dtype=np.int64)
+    for j, d in enumerate(deltas):
+        q[j] = (q[j - 2] if j >= 2 else 0) + d
+    xr = q.astype(np.float64) * (2 * eb)
+    mine = oracle.decompress_block(s, b, oracle.C128, eb, chunk=chunk)
+    assert np.array_equal(xr[0::2], mine.real) and np.array_equal(xr[1::2], mine.imag)
     base = oracle.decompress_block(oracle.compress_block(v, b, oracle.C128, eb)[0], b, oracle.C128, eb)
     got = oracle.decompress_block(s, b, oracle.C128, eb, chunk=chunk)
     assert got.tobytes() == base.tobytes()
