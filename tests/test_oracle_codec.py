@@ -284,3 +284,34 @@ def test_chunk_table_matches_an_independent_decode(chunk, kind, eb):
     base = oracle.decompress_block(oracle.compress_block(v, b, oracle.C128, eb)[0], b, oracle.C128, eb)
     got = oracle.decompress_block(s, b, oracle.C128, eb, chunk=chunk)
     assert got.tobytes() == base.tobytes()
+
+
+@pytest.mark.parametrize("dtype", [oracle.C128, oracle.C64])
+def test_pack_mode_matches_an_independent_decode(dtype):
+    # PACK: every delta as a zigzag code (0, -1, 1, -2, 2, ... -> 0, 1, 2, 3, 4, ...) of
+    # `width` bits, MSB-first in little-endian u32 words; values by the per-plane Lorenzo rule
+    b = 8
+    eb = 1e-8 if dtype == oracle.C128 else 1e-5  # complex64: float rounding stays inside eb
+    rng = np.random.default_rng(23)
+    v = gen_block("wide", b, rng, dtype)
+    s, info = oracle.compress_block(v, b, dtype, eb)
+    mode, dt, bl, width, nverb, D = struct.unpack_from("<BBBBHH", s, 0)
+    assert mode == oracle.MODE_PACK and nverb == 0
+    pbits, total = struct.unpack_from("<II", s, 8)
+    nv = 2 << b
+    assert pbits == nv * width and total == len(s) and 1 <= width <= 32
+    words = struct.unpack_from("<%dI" % ((pbits + 31) // 32), s, 16)
+    bits = "".join(format(w, "032b") for w in words)
+    q = np.zeros(nv, dtype=np.int64)
+    for j in range(nv):
+        z = int(bits[j * width:(j + 1) * width], 2)
+        d = (z >> 1) if z % 2 == 0 else -((z + 1) >> 1)
+        q[j] = (q[j - 2] if j >= 2 else 0) + d
+    x = q.astype(np.float64) * (2 * eb)
+    if dtype == oracle.C64:
+        x = x.astype(np.float32)
+    mine = oracle.decompress_block(s, b, dtype, eb)
+    assert np.array_equal(x[0::2], mine.real) and np.array_equal(x[1::2], mine.imag)
+    # and the width is the smallest that holds the largest zigzag code
+    zmax = max(int(bits[j * width:(j + 1) * width], 2) for j in range(nv))
+    assert zmax.bit_length() == width
