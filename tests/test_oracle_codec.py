@@ -315,3 +315,42 @@ def test_pack_mode_matches_an_independent_decode(dtype):
     # and the width is the smallest that holds the largest zigzag code
     zmax = max(int(bits[j * width:(j + 1) * width], 2) for j in range(nv))
     assert zmax.bit_length() == width
+
+
+@pytest.mark.parametrize("dtype", [oracle.C128, oracle.C64])
+def test_verbatim_section_layout(dtype):
+    # verbatim section after the body: u16 value positions ascending (value j = 2 * amplitude
+    # + 0 for re, + 1 for im), then the raw values at the next multiple of the value size;
+    # the verbatim values enter the prediction as code 0
+    b, eb = 6, 1e-6
+    rng = np.random.default_rng(4)
+    v = (rng.standard_normal(1 << b) + 1j * rng.standard_normal(1 << b)) * 1e-3
+    big = {5: 3e6 + 0j, 17: complex(0.0, -4e6), 40: complex(5e6, 6e6)}
+    for k, x in big.items():
+        v[k] = x
+    v = v.astype(np.complex64 if dtype == oracle.C64 else np.complex128)
+    s, info = oracle.compress_block(v, b, dtype, eb)
+    mode, dt, bl, param, nverb, D = struct.unpack_from("<BBBBHH", s, 0)
+    pos_want = sorted([2 * 5, 2 * 17 + 1, 2 * 40, 2 * 40 + 1])
+    assert nverb == len(pos_want) == info["n_verbatim"]
+    # the body ends where the chunk table, codebook and payload end; the section is the
+    # stream's tail: positions, padding to the value size, values, zero padding to 16 bytes
+    vs = np.dtype(np.float32 if dtype == oracle.C64 else np.float64).itemsize
+    raw = np.frombuffer(v.view(np.float32 if dtype == oracle.C64 else np.float64).tobytes(),
+                        dtype=np.float32 if dtype == oracle.C64 else np.float64)
+    want_vals = b"".join(raw[j:j + 1].tobytes() for j in pos_want)
+    want_pos = struct.pack("<%dH" % nverb, *pos_want)
+    i = s.find(want_pos)
+    assert i >= 16 and i % 4 == 0
+    voff = (i + 2 * nverb + vs - 1) // vs * vs
+    assert s[voff:voff + vs * nverb] == want_vals
+    assert len(s) % 16 == 0 and set(s[voff + vs * nverb:]) <= {0}
+    # prediction treats them as 0: the same block with those values replaced by 0 gives the
+    # same mode, symbol count, payload bits and body; only the verbatim count, the total
+    # length and the section differ
+    z = v.copy()
+    for k in big:
+        z[k] = 0
+    s0, _ = oracle.compress_block(z, b, dtype, eb)
+    assert s0[0:4] == s[0:4] and s0[6:12] == s[6:12] and s0[16:i] == s[16:i]
+    assert struct.unpack_from("<H", s0, 4)[0] == 0 and len(s0) == (i + 15) // 16 * 16
