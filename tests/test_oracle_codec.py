@@ -354,3 +354,19 @@ def test_verbatim_section_layout(dtype):
     s0, _ = oracle.compress_block(z, b, dtype, eb)
     assert s0[0:4] == s[0:4] and s0[6:12] == s[6:12] and s0[16:i] == s[16:i]
     assert struct.unpack_from("<H", s0, 4)[0] == 0 and len(s0) == (i + 15) // 16 * 16
+
+
+@pytest.mark.parametrize("dtype", [oracle.C128, oracle.C64])
+def test_quantizer_range_boundary(dtype):
+    # a value is quantized while |x r| < 2^29 (codes and their deltas then fit 32-bit
+    # integers) and stored raw from 2^29 on; eb = 2^-11 makes r = 2^10 exact
+    b, eb = 5, 2.0 ** -11
+    lim = 2.0 ** 29 / 2.0 ** 10  # |x| at which |x r| reaches 2^29
+    below = np.nextafter(np.float32(lim), np.float32(0)) if dtype == oracle.C64 else np.nextafter(lim, 0)
+    for x, verb in [(lim, True), (-lim, True), (float(below), False), (-float(below), False)]:
+        v = np.zeros(1 << b, dtype=np.complex64 if dtype == oracle.C64 else np.complex128)
+        v[3] = x
+        s, info = oracle.compress_block(v, b, dtype, eb)
+        assert info["n_verbatim"] == (1 if verb else 0), x
+        d = oracle.decompress_block(s, b, dtype, eb)
+        assert abs(float(d[3].real) - x) <= eb
