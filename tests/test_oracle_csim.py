@@ -226,3 +226,19 @@ def test_stored_norm_counts_verbatim_values(dtype):
     fp = (1e-15 if dtype == oracle.C128 else 6e-7) * np.abs(y).max()
     assert np.abs(got - y).max() <= math.sqrt(2) * eb + fp
     assert abs(cs.norm - np.vdot(got, got).real) <= rel * cs.norm
+
+
+@pytest.mark.parametrize("n,eb", [(10, 1e-5), (12, 1e-6), (13, 1e-7)])
+def test_qft_infidelity_matches_the_first_order_model(n, eb):
+    # Rounding to the 2eb grid adds a uniform error in [-eb, eb] to each component of every
+    # freshly quantized value: eb^2/3 per component, (2/3) eb^2 per complex value, almost all
+    # of it orthogonal to the state. QFT of a basis state freshly quantizes about 2.5 * 2^n
+    # values over the circuit (each stage's H, and the controlled phases where the control is
+    # set; SWAPs and identities stay on the grid), so 1 - F ~ 2.5 * 2^n * (2/3) eb^2. O2 must
+    # land within 20 % of it (truncating instead of rounding would quadruple it).
+    x = C.seeded_index(0, n)
+    cs = oracle.CompressedSim(n, 8, 8, oracle.C128, eb, x).run(C.qft(n))
+    ref = np.exp(2j * np.pi * ((x * np.arange(1 << n)) % (1 << n)) / (1 << n)) / 2 ** (n / 2)
+    measured = 1.0 - fidelity(cs.read(), ref)
+    model = 2.5 * (1 << n) * (2.0 / 3.0) * eb * eb
+    assert 0.8 < measured / model < 1.2, (measured, model)
