@@ -242,3 +242,20 @@ def test_qft_infidelity_matches_the_first_order_model(n, eb):
     measured = 1.0 - fidelity(cs.read(), ref)
     model = 2.5 * (1 << n) * (2.0 / 3.0) * eb * eb
     assert 0.8 < measured / model < 1.2, (measured, model)
+
+
+def test_stored_norm_beyond_64_bits():
+    # codes near the quantizer's limit (|q| ~ 2^28): Σq² over 2^10 values exceeds 2^64, so the
+    # exact integer sum needs its high word; N must still be the squared norm of the values
+    n, sl, b = 9, 9, 8
+    eb = 2.0 ** -11
+    lim = 2.0 ** 29 / 2.0 ** 10
+    rng = np.random.default_rng(29)
+    v = (rng.uniform(0.4, 0.9, 1 << n) * np.exp(2j * np.pi * rng.random(1 << n))) * lim
+    cs = oracle.CompressedSim(n, sl, b, oracle.C128, eb)
+    cs.load(v)
+    x = cs.read()
+    q2 = np.sum(np.round(x.real * 2 ** 10) ** 2 + np.round(x.imag * 2 ** 10) ** 2)
+    assert q2 > 2.0 ** 64
+    N = cs.norm
+    assert abs(N - np.vdot(x, x).real) <= 1e-12 * N
