@@ -155,17 +155,29 @@ int sv_batch_apply(sv_batch* batch, sv_state* const* states, const sv_gate_t* ga
 int sv_sync(sv_state* s);
 
 /* ---------------------------------------------------------------------------------------
- * Measurements (synchronizing).
+ * Measurements (synchronizing). The paper judges a compressed simulation by the fidelity of
+ * its final state to the uncompressed simulator's and by the compression ratio, whose minimum
+ * over a run sets how many extra qubits fit in memory (Sec. III; the ratio as the measure of
+ * the method's scalability: Sec. I). Arguments are host pointers owned by the caller; errors:
+ * SV_ERR_ARG for bad arguments, SV_ERR_NORM when the state's norm is zero, otherwise any error
+ * the state has recorded on the device.
  * sv_measure_probs: marginal probabilities of the m (<= 14) given qubits of the normalized
- *   stored state; out[2^m] (host), out[v] = P(bits of the listed qubits = v, qubits[0]
- *   least significant).
+ *   stored state (the Born rule on the state Sec. II keeps, normalized by its stored norm N);
+ *   out[2^m] (host), out[v] = P(bits of the listed qubits = v, qubits[0] least significant).
+ *   The paper prints no probabilities; for its QFT benchmark (Sec. III) on a basis state
+ *   every outcome has probability 2^-n, which these marginals check.
  * sv_amplitudes: the stored (reconstructed, not rescaled) amplitudes x' at host indices
  *   idx[] into out[2*cnt] (re, im FP64). The stored state has norm sv_norm(); multiply by
  *   1/sqrt(norm) for the normalized amplitudes.
  * sv_read_amplitudes: stored amplitudes [start, start+count) into host out[2*count].
- * sv_fidelity: |<a|b>|^2 / (<a|a><b|b>) of two states of equal n (either path).
- * sv_compressed_bytes: bytes of all block streams of the current state (plain path: the
- *   vector's bytes).
+ * sv_fidelity: F = |<a|b>|^2 / (<a|a><b|b>) of two states of equal n (either path), the
+ *   state fidelity of Sec. III (1 for identical states) in its squared pure-state form; the
+ *   paper compares the compressed run's final amplitudes with the original simulator's,
+ *   which is this call with b on the plain path (error_bound 0). *out receives F.
+ * sv_compressed_bytes: bytes of all block streams of the current state (headers, codebooks,
+ *   payload, verbatim values; plain path: the vector's bytes). The compression ratio of
+ *   Sec. I / III is 2^(n+4) (complex128) or 2^(n+3) (complex64) divided by this; the paper
+ *   reports its minimum over the run (Sec. III), i.e. this call after every gate.
  * ------------------------------------------------------------------------------------- */
 int sv_measure_probs(sv_state* s, const int* qubits, int m, double* out);
 int sv_amplitudes(sv_state* s, const uint64_t* idx, size_t cnt, double* out);
@@ -218,7 +230,8 @@ int sv_block_stream(sv_state* s, uint64_t b, uint8_t* out, size_t cap, size_t* l
  * sv_codec_decompress: the inverse, from device streams at in + offsets[i] into device
  *   `values`. SV_ERR_CORRUPT when a stream fails the bounds checks.
  * Both synchronize `stream`. The scratch they need (a few counters) is the caller's
- *   `scratch` device buffer of at least sv_codec_scratch_bytes() bytes.
+ *   `scratch` device buffer of at least sv_codec_scratch_bytes() bytes. nblocks == 0 is a
+ *   no-op that returns SV_OK (compress: *used = 0).
  * ------------------------------------------------------------------------------------- */
 size_t sv_codec_scratch_bytes(void);
 int sv_codec_compress(const void* values, uint64_t nblocks, int block_log2, int dtype,
@@ -243,10 +256,15 @@ int sv_codec_decompress(const void* in, const uint64_t* offsets, const uint32_t*
  * exact sum of the squared codes and V the pairwise sum of the per-block squares of the
  * verbatim values (list padded with zeros to a power of two).
  * The first call on a device looks the array's device address up (once per device, with
- * that device current); make that first call before any stream capture. Every call clears
- * the record it uses at its start; the array is shared by all calls on a device and keeps
- * the last call's contents, so calls that overlap on the GPU (other streams or threads)
- * race and must be serialized by the caller. Synchronizes `stream`. No memory is allocated.
+ * that device current) and caches it for the life of the process; after a cudaDeviceReset
+ * of that device the cached address is stale, so do not call this function on a device the
+ * process has reset. Every call clears the record it uses at its start; the array is shared
+ * by all calls on a device and keeps the last call's contents, so calls that overlap on the
+ * GPU (other streams or threads) race and must be serialized by the caller. Every call reads
+ * its results back and synchronizes `stream`, so it cannot be recorded into a CUDA graph: on a
+ * stream that is capturing (or whose capture state cannot be read) it returns SV_ERR_ARG
+ * before enqueueing anything. nblocks == 0: SV_OK with *used = 0 and *norm = 0, nothing
+ * launched. No memory is allocated.
  * ------------------------------------------------------------------------------------- */
 #define SV_STATIC_MAX_BLOCKS 65536
 int sv_codec_compress_static(const void* values, uint64_t nblocks, int block_log2, int dtype,

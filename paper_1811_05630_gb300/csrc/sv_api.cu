@@ -419,15 +419,20 @@ int ensure_aux(sv_state* s) {
   return SV_OK;
 }
 
-// Decoded FP64 amplitudes [start, start+count) (count <= chunk_amps) into dst (device).
-int read_chunk(sv_state* s, unsigned long long start, unsigned long long count, double* dst) {
-  if (s->plain) return cuda_err(launch_plain_read(s->psi, s->dtype == SV_C64 ? 1 : 2, start, count, dst, s->st));
+// Decoded FP64 amplitudes [start, start+count) (count <= chunk_amps) into dst (device), on
+// stream `st` (the state's own stream unless a caller has ordered st after it).
+int read_chunk(sv_state* s, unsigned long long start, unsigned long long count, double* dst,
+               cudaStream_t st) {
+  if (s->plain) return cuda_err(launch_plain_read(s->psi, s->dtype == SV_C64 ? 1 : 2, start, count, dst, st));
   const unsigned long long B = 1ull << s->b;
   const unsigned long long b0 = start / B, b1 = (start + count + B - 1) / B;
   // chunk sizes are multiples of B (start, count aligned by the callers)
   cudaError_t e = launch_read_blocks(s->arena[s->cur], s->toff[s->cur], s->tlen[s->cur], b0, b1 - b0,
-                                     s->b, s->dtype == SV_C64 ? 1 : 2, s->qp, dst, s->sc, s->st);
+                                     s->b, s->dtype == SV_C64 ? 1 : 2, s->qp, dst, s->sc, st);
   return cuda_err(e);
+}
+int read_chunk(sv_state* s, unsigned long long start, unsigned long long count, double* dst) {
+  return read_chunk(s, start, count, dst, s->st);
 }
 
 int check_status(sv_state* s) {
@@ -866,17 +871,23 @@ int sv_fidelity(sv_state* a, sv_state* b, double* out) {
   rc = ensure_aux(a);
   if (!rc) rc = ensure_aux(b);
   if (rc) return rc;
-  // work on a's stream; b's reads are ordered after b's own work by the sync above
+  // work on a's stream: b's blocks are read there too, after an event that orders a's stream
+  // behind everything submitted on b's (b itself is not modified)
+  if (b->st != a->st) {
+    cudaEvent_t ev = nullptr;
+    cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(ev, b->st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(a->st, ev, 0);
+    if (ev) cudaEventDestroy(ev);
+    if (e != cudaSuccess) return cuda_err(e);
+  }
   const unsigned long long dim = 1ull << a->n;
   const unsigned long long ch = std::min(a->chunk_amps, b->chunk_amps);
   cudaMemsetAsync(a->acc, 0, 4 * sizeof(double), a->st);
   for (unsigned long long st = 0; st < dim; st += ch) {
     rc = read_chunk(a, st, ch, a->chunk[0]);
     if (rc) return rc;
-    cudaStream_t keep = b->st;
-    b->st = a->st;
-    rc = read_chunk(b, st, ch, a->chunk[1]);
-    b->st = keep;
+    rc = read_chunk(b, st, ch, a->chunk[1], a->st);
     if (rc) return rc;
     cudaError_t e = launch_dot_chunk(a->chunk[0], a->chunk[1], ch, a->acc, a->st);
     if (e != cudaSuccess) return cuda_err(e);
@@ -1140,6 +1151,10 @@ int sv_codec_compress(const void* values, uint64_t nblocks, int bl, int dtype, d
       (dtype != SV_C64 && dtype != SV_C128) || !(eb > 0.0) || !std::isfinite(eb) ||
       ((uintptr_t)out & 15) || ((uintptr_t)scratch & 15))
     return SV_ERR_ARG;
+  if (nblocks == 0) {  // nothing to compress
+    if (used) *used = 0;
+    return SV_OK;
+  }
   cudaStream_t st = (cudaStream_t)stream;
   DevScalars* sc = (DevScalars*)scratch;
   QuantP qp;
@@ -1166,6 +1181,7 @@ int sv_codec_decompress(const void* in, const uint64_t* offsets, const uint32_t*
       (dtype != SV_C64 && dtype != SV_C128) || !(eb > 0.0) || !std::isfinite(eb) ||
       ((uintptr_t)in & 15) || ((uintptr_t)scratch & 15))
     return SV_ERR_ARG;
+  if (nblocks == 0) return SV_OK;  // nothing to decode
   cudaStream_t st = (cudaStream_t)stream;
   DevScalars* sc = (DevScalars*)scratch;
   QuantP qp;

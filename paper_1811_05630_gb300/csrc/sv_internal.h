@@ -1,11 +1,27 @@
 // sv_internal.h — launchers shared by the host API and the kernels translation unit.
 #pragma once
 #include <cuda_runtime.h>
+#include <atomic>
 #include <cstdint>
 
 #include "sv_block.cuh"
 
 namespace sv {
+
+// Per-device one-time setup of a kernel's launch attributes: `done` is a bit set over device
+// ordinals (0..63) owned by the caller (one per kernel instantiation). Returns the error of the
+// first failing setup call, cudaSuccess once the current device is set up.
+template <typename F>
+inline cudaError_t once_per_device(std::atomic<unsigned long long>& done, F setup) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = dev < 64 ? (1ull << dev) : 0ull;
+  if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+  e = setup();
+  if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_acq_rel);
+  return e;
+}
 
 // Fused gate pass (Algorithm 1 over every slice) for one state; Real by dtype (1 = float).
 cudaError_t launch_pass(const PassArgs& a, int dtype, cudaStream_t st);

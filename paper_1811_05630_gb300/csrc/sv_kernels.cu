@@ -135,12 +135,11 @@ static cudaError_t launch_pass_batch_k(const PassArgs* descs, const unsigned lon
                                        unsigned long long total_groups, int b, int Gmax, int threads, int chunk,
                                        cudaStream_t st) {
   const Layout L = make_layout(b, Gmax, (int)sizeof(Real), true);  // the kernel's layout
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_pass_batch<Real, KM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  static std::atomic<unsigned long long> configured{0};  // devices set up
+  cudaError_t ce = once_per_device(configured, [] {
+    return cudaFuncSetAttribute(k_pass_batch<Real, KM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  });
+  if (ce != cudaSuccess) return ce;
   if (L.total > 227 * 1024) return cudaErrorInvalidValue;
   const int T = threads_ok(b, threads) ? threads : worker_threads(b);
   if (!chunk_ok(b, chunk, T)) return cudaErrorInvalidValue;

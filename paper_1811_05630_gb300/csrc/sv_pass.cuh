@@ -493,14 +493,12 @@ __global__ void __launch_bounds__(256, 4) k_pass_c(const PassArgs a) {
 template <typename Real, int KM, bool COMPACT>
 static cudaError_t launch_pass_k(const PassArgs& a, cudaStream_t st) {
   const Layout L = make_layout(a.b, a.G, (int)sizeof(Real));
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e;
-    if constexpr (COMPACT) e = cudaFuncSetAttribute(k_pass_c<Real, KM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    else e = cudaFuncSetAttribute(k_pass<Real, KM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  static std::atomic<unsigned long long> configured{0};  // devices set up
+  cudaError_t ce = once_per_device(configured, [] {
+    if constexpr (COMPACT) return cudaFuncSetAttribute(k_pass_c<Real, KM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    else return cudaFuncSetAttribute(k_pass<Real, KM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  });
+  if (ce != cudaSuccess) return ce;
   if (L.total > 227 * 1024) return cudaErrorInvalidValue;
   const int T = threads_ok(a.b, a.threads) ? a.threads : worker_threads(a.b);
   if (!chunk_ok(a.b, a.chunk ? a.chunk : kChunkDefault, T)) return cudaErrorInvalidValue;

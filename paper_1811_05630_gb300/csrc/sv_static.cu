@@ -3,16 +3,18 @@
 // sv_codec_compress needs a small caller-provided scratch buffer (a bump counter, status
 // flags and statistics). Some callers cannot provide one: code that runs where device
 // allocation is forbidden or unavailable (inside a region whose memory was fixed up front,
-// in a runtime that owns every allocation, or between a stream's capture points where an
-// allocation would not be recorded). sv_codec_compress_static does the same compression
-// with its scratch in a fixed array compiled into the library instead, and also reports the
-// stored norm of what it compressed. It allocates nothing.
+// or in a runtime that owns every allocation). sv_codec_compress_static does the same
+// compression with its scratch in a fixed array compiled into the library instead, and also
+// reports the stored norm of what it compressed. It allocates nothing.
 //
 // The array is shared by every call on a device and keeps the last call's contents; each
 // call clears the part that must start at zero. Calls that overlap on the GPU (two streams,
-// or two host threads) race on it and must be serialized by the caller.
+// or two host threads) race on it and must be serialized by the caller. Every call reads its
+// results back to the host and synchronizes the stream, so it cannot be recorded into a CUDA
+// graph: a call on a stream that is capturing is refused (SV_ERR_ARG) before any work.
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <mutex>
 
 #include "../../include/sv.h"
@@ -34,7 +36,9 @@ constexpr int kMaxDevices = 64;
 void* g_dev_ptr[kMaxDevices] = {nullptr};
 std::mutex g_mu;
 
-// Device address of g_scratch on the current device (looked up once per device).
+// Device address of g_scratch on the current device (looked up once per device, then
+// cached for the life of the process: after a cudaDeviceReset the cached address is stale,
+// so a process that resets a device must not call this entry point on it again).
 cudaError_t scratch_ptr(void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -88,13 +92,27 @@ extern "C" int sv_codec_compress_static(const void* values, uint64_t nblocks, in
                                         uint32_t* lengths, void* stream, uint64_t* used,
                                         double* norm) {
   if (!values || !out || !offsets || !lengths || bl < 5 || bl > 12 ||
-      (dtype != SV_C64 && dtype != SV_C128) || !(eb > 0.0) || !(eb < 1e300) || ((uintptr_t)out & 15))
+      (dtype != SV_C64 && dtype != SV_C128) || !(eb > 0.0) || !std::isfinite(eb) || ((uintptr_t)out & 15))
     return SV_ERR_ARG;
-  if (nblocks == 0 || nblocks > kMaxBlocks) return SV_ERR_UNSUPPORTED;
+  if (nblocks > kMaxBlocks) return SV_ERR_UNSUPPORTED;
+  cudaStream_t st = (cudaStream_t)stream;
+  // the call ends with a read-back and a stream synchronization, neither of which a capturing
+  // stream accepts: refuse before enqueueing anything (an error here means the stream's
+  // capture state could not be read, e.g. the legacy stream while another stream captures)
+  cudaStreamCaptureStatus cap_st = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap_st) != cudaSuccess) {
+    cudaGetLastError();
+    return SV_ERR_ARG;
+  }
+  if (cap_st != cudaStreamCaptureStatusNone) return SV_ERR_ARG;
+  if (nblocks == 0) {  // nothing to compress (the same result as sv_codec_compress)
+    if (used) *used = 0;
+    if (norm) *norm = 0.0;
+    return SV_OK;
+  }
   void* base = nullptr;
   cudaError_t e = scratch_ptr(&base);
   if (e != cudaSuccess) return SV_ERR_CUDA;
-  cudaStream_t st = (cudaStream_t)stream;
   DevScalars* sc = (DevScalars*)base;
   double* vsum = (double*)((unsigned char*)base + kRecordBytes);
   double* nout = vsum + kMaxBlocks;

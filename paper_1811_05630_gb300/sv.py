@@ -319,13 +319,23 @@ def codec_compress_static(values: torch.Tensor, block_log2: int, error_bound: fl
     every buffer passed here and the library uses its own fixed scratch array (no scratch
     argument, nothing allocated). Returns (used bytes, stored norm of the compressed values)."""
     assert values.is_cuda and values.is_contiguous()
+    assert values.dtype in (torch.complex64, torch.complex128)
     dtype = C64 if values.dtype == torch.complex64 else C128
     nblocks = values.numel() >> block_log2
+    # the C side takes no buffer lengths and its scratch is per device: check here what it
+    # cannot (every buffer on the values' device, long enough, of the declared type)
+    assert nblocks << block_log2 == values.numel(), "length must be a multiple of 2^block_log2"
+    assert out.dtype == torch.uint8 and out.is_contiguous()
+    assert offsets.dtype == torch.int64 and offsets.is_contiguous() and offsets.numel() >= nblocks
+    assert lengths.dtype == torch.int32 and lengths.is_contiguous() and lengths.numel() >= nblocks
+    for t in (out, offsets, lengths):
+        assert t.device == values.device, "every buffer must be on the device of `values`"
     used, norm = ctypes.c_uint64(), ctypes.c_double()
-    _check(_L.sv_codec_compress_static(values.data_ptr(), nblocks, block_log2, dtype, float(error_bound),
-                                       out.data_ptr(), out.numel(), offsets.data_ptr(), lengths.data_ptr(),
-                                       _stream_handle(stream), ctypes.byref(used), ctypes.byref(norm)),
-           "sv_codec_compress_static")
+    with torch.cuda.device(values.device):
+        _check(_L.sv_codec_compress_static(values.data_ptr(), nblocks, block_log2, dtype, float(error_bound),
+                                           out.data_ptr(), out.numel(), offsets.data_ptr(), lengths.data_ptr(),
+                                           _stream_handle(stream), ctypes.byref(used), ctypes.byref(norm)),
+               "sv_codec_compress_static")
     return used.value, norm.value
 
 

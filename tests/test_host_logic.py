@@ -318,15 +318,20 @@ def test_traffic_record_needs_matching_sources_and_shape(monkeypatch, tmp_path):
     prof = tmp_path / "profiles"
     prof.mkdir()
     (prof / "k_pass_demo.md").write_text(
-        "text\nTRAFFIC digest=abc block_log2=11 threads=256 compact=1 bytes_per_launch=123 launches=x_y\n")
+        "text\nTRAFFIC digest=abc block_log2=11 threads=256 compact=1 window=586-606 bytes_per_launch=123 "
+        "launches=x_y\n")
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     monkeypatch.setattr(bench, "source_digest", lambda: "abc")
-    assert bench.recorded_traffic("demo", 11, 256, True) == (123.0, "x y")
-    assert bench.recorded_traffic("demo", 10, 256, True)[0] is None
-    assert bench.recorded_traffic("demo", 11, 256, False)[0] is None
+    assert bench.recorded_traffic("demo", 11, 256, True, window="586-606") == (123.0, "x y")
+    assert bench.recorded_traffic("demo", 10, 256, True, window="586-606")[0] is None
+    assert bench.recorded_traffic("demo", 11, 256, False, window="586-606")[0] is None
+    # a capture of another window of passes does not describe this run's launches
+    assert bench.recorded_traffic("demo", 11, 256, True, window="25-45") == (
+        None, "no ncu capture of this window of passes")
     monkeypatch.setattr(bench, "source_digest", lambda: "def")
-    assert bench.recorded_traffic("demo", 11, 256, True) == (None, "kernel sources changed since the ncu capture")
-    assert bench.recorded_traffic("other", 11, 256, True)[0] is None
+    assert bench.recorded_traffic("demo", 11, 256, True, window="586-606") == (
+        None, "kernel sources changed since the ncu capture")
+    assert bench.recorded_traffic("other", 11, 256, True, window="586-606")[0] is None
 
 
 def test_clock_summary_reads_throttle_reasons():
@@ -355,4 +360,32 @@ def test_dense_stage_start():
     gates = C.qft(34)
     i0 = bench.start_of_dense_stage(wl)
     assert gates[i0].name == "H" and gates[i0].targets == (10,)
-    assert bench.start_of_dense_stage({"name": "grover20", "n": 20, "block_log2": 11}) == 20
+    # Grover: the first H of the first diffusion, after the initial H layer and the oracle
+    # (X on the marked item's zero bits, MCZ, X again): before it every block is constant
+    marked = C.seeded_index(11, 20)
+    g20 = C.grover(20, marked)
+    i0 = bench.start_of_dense_stage({"name": "grover20", "n": 20, "block_log2": 10, "marked": marked})
+    zeros = [q for q in range(20) if not (marked >> q) & 1]
+    assert i0 == 20 + 2 * len(zeros) + 1
+    assert [g.name for g in g20[i0:i0 + 20]] == ["H"] * 20 and g20[i0 - 1].name == "X"
+    assert g20[i0 - len(zeros) - 1].name == "MCZ"
+
+
+def test_qft_window_ends_at_the_last_recoding_pass():
+    import bench
+
+    wl = bench.workload("qft34")
+    b = wl["block_log2"]
+    w0, t0, t1 = bench.timed_window(wl, 20, 5)
+    g = wl["gates"]
+    assert (t0 - w0, t1 - t0) == (5, 20)
+    # the passes after the window are SWAPs of two qubits at or above the block (they move whole
+    # blocks and re-emit every stream); every pass of the window recodes blocks
+    assert all(x.name == "SWAP" and min(x.targets) >= b for x in g[t1:])
+    assert all(bench.recodes_every_block(x, b) for x in g[w0:t1])
+    assert g[t1 - 1].name == "SWAP" and g[t1 - 1].targets == (b - 1, 34 - b)
+    # the window lies in the dense stage (every block holds more than one nonzero value)
+    assert w0 >= bench.start_of_dense_stage(wl)
+    assert {x.name for x in g[t0:t1]} >= {"H", "SWAP"}
+    with pytest.raises(ValueError):
+        bench.timed_window(wl, 700, 5)
