@@ -222,6 +222,14 @@ def grover_fidelity(st, wl, iters):
     return abs(ov) ** 2 / np.vdot(v, v).real, abs(v[m]) ** 2 / np.vdot(v, v).real
 
 
+def log(msg: str) -> None:
+    """Progress on stderr (the JSON line is the only stdout output)."""
+    print("[bench %.0f s] %s" % (time.time() - T_START, msg), file=sys.stderr, flush=True)
+
+
+T_START = time.time()
+
+
 def max_over_ranks(x: float, dist) -> float:
     """The largest x over the ranks of the process group (x itself without one): replicas are
     timed each on its own GPU and the job takes as long as the slowest."""
@@ -406,6 +414,7 @@ def run_ours(args, rank, world, dist):
     st.run(gates[:t0])  # untimed: the circuit up to the window, then the warm-up passes
     st.sync()
     t_setup = time.time() - t_setup
+    log("reached pass %d in %.1f s (compressed %d bytes)" % (t0, t_setup, st.compressed_bytes()))
     timed = gates[t0:t1]
     b = wl["block_log2"]
     st.set_pass_timing(True)
@@ -474,6 +483,16 @@ def run_ours(args, rank, world, dist):
                        "from the decoded state"}
     t_rest = time.time() - t_rest
     pool_used = pool.usage()[0]
+    # release the compressed state's pool before the plain vector and the serving run
+    st.close()
+    pool.close()
+    del st, pool
+    import gc
+
+    gc.collect()
+    torch.cuda.empty_cache()
+    log("timed window done: %.3g amp-updates/s, setup %.0f s, rest %.0f s, fidelity %s"
+        % (value, t_setup, t_rest, fid and fid.get("one_minus_F")))
 
     result = None
     if rank == 0:
@@ -494,18 +513,12 @@ def run_ours(args, rank, world, dist):
                 if "fallback" not in pk else "fallback 6.8 TB/s"}
         cpu = (cpu_oracle_sample(wl, args.steps, args.warmup, budget_s=args.cpu_budget)
                if args.cpu_budget > 0 else None)
+        log("cpu baseline: %s" % (cpu and cpu["value"]))
         # plain GPU path on the same gates, where its vector fits: its time does not depend on
         # the amplitudes' values, so it runs from the basis state
         plain = None
         if args.plain:
             try:
-                st.close()
-                pool.close()
-                del pool
-                import gc
-
-                gc.collect()
-                torch.cuda.empty_cache()
                 ppool = sv.Pool(((16 if wl["dtype"] == 2 else 8) << n) + (64 << 20))
                 ps = sv.State(ppool, n, n, 0.0, wl["dtype"])
                 ps.reset_basis(wl["basis"])
@@ -523,11 +536,24 @@ def run_ours(args, rank, world, dist):
                 plain = (1 << n) * len(timed) / (pms * 1e-3)
                 ps.close()
                 ppool.close()
+                del ps, ppool
             except Exception as ex:  # noqa: BLE001
                 plain = "unavailable: %s" % ex
+            log("plain path: %s" % plain)
         del flush
         if fid is None and args.fidelity and wl["name"] == "grover20":
             fid = full_grover_fidelity(sv, wl)
+        serving = None
+        if args.serve_in_bench > 0:
+            gc.collect()
+            torch.cuda.empty_cache()
+            try:
+                serving = serving_run(args.serve_in_bench, args.serve_rate, args.serve_in_bench_limit,
+                                      args.pool_gb or 150.0, args.serve_budget_gb)
+                log("serving: p50 %s p99 %s completed %d censored %d" % (
+                    serving["p50_s"], serving["p99_s"], serving["completed"], serving["censored"]))
+            except Exception as ex:  # noqa: BLE001
+                serving = {"error": "%s: %s" % (type(ex).__name__, ex)}
         launches_per_pass = 2  # the fused pass and the one-CTA norm kernel
         raw = report.raw_state_bytes(n, wl["dtype"])
         result = {
@@ -555,6 +581,7 @@ def run_ours(args, rank, world, dist):
                        "fidelity": fid},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
             "gpu_launches": launches_per_pass * len(timed),
+            "serving": serving,
         }
     return result
 
@@ -701,16 +728,18 @@ def run_full_circuit(args):
     return res
 
 
-def run_serving(args):
-    """The mixed request stream (2000 Poisson requests at 20/s by default) through the
-    continuous-batching loop for --serve-seconds of wall time."""
+def serving_run(count: int, rate: float, time_limit: float, pool_gb: float, budget_gb: float):
+    """The mixed request stream through the continuous-batching loop: the first `count`
+    requests of the seeded stream (Poisson arrivals at `rate` per second; QFT / Grover /
+    brickwork, 10-28 qubits, both dtypes, three bounds), until every one is done or the time
+    limit; requests still queued or running at the limit are counted as censored."""
     from paper_1811_05630_gb300.serve import Server, size_class
 
-    reqs = C.serving_requests(count=args.serve_count, rate=args.serve_rate, seed=0)
-    srv = Server(pool_bytes=int((args.pool_gb or 150.0) * (1 << 30)), budget_bytes=int(args.serve_budget_gb * 1e9),
+    reqs = C.serving_requests(count=count, rate=rate, seed=0)
+    srv = Server(pool_bytes=int(pool_gb * (1 << 30)), budget_bytes=int(budget_gb * 1e9),
                  block_log2=10, max_batch=64, graphs=True)
-    with ClockSampler(0) as clk:
-        out = srv.run(reqs, time_limit=args.serve_seconds)
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        out = srv.run(reqs, time_limit=time_limit)
     res = out.pop("results")
     out["failed_requests"] = [{"rid": r.rid, "kind": reqs[r.rid].kind, "n": reqs[r.rid].n,
                                "dtype": reqs[r.rid].dtype, "eb": reqs[r.rid].eb, "error": r.error}
@@ -719,20 +748,27 @@ def run_serving(args):
     for r in res:
         if r.error:
             continue
-        c = size_class(reqs[r.rid].n)
-        by.setdefault(c, []).append(r.latency)
-    out["completed_by_size_class"] = {["n<=16", "17-22", "23-28"][c]: len(v) for c, v in sorted(by.items())}
-    out["p50_s_by_size_class"] = {["n<=16", "17-22", "23-28"][c]: float(np.percentile(v, 50)) for c, v in sorted(by.items())}
-    out["p99_s_by_size_class"] = {["n<=16", "17-22", "23-28"][c]: float(np.percentile(v, 99)) for c, v in sorted(by.items())}
-    arrived = sum(1 for r in reqs if r.arrival <= out["wall_s"])
-    out["arrived_within_limit"] = arrived
-    out["offered_within_limit_amp_updates_per_s"] = sum(r.amp_updates for r in reqs if r.arrival <= out["wall_s"]) / out["wall_s"]
-    out["config"] = {"requests": args.serve_count, "rate_per_s": args.serve_rate, "budget_gb": args.serve_budget_gb,
-                     "time_limit_s": args.serve_seconds, "block_log2": 10, "threads_per_cta": 128, "max_batch": 64,
-                     "graphs": True}
+        by.setdefault(size_class(reqs[r.rid].n), []).append(r.latency)
+    names = ["n<=16", "17-22", "23-28"]
+    out["completed_by_size_class"] = {names[c]: len(v) for c, v in sorted(by.items())}
+    out["p50_s_by_size_class"] = {names[c]: float(np.percentile(v, 50)) for c, v in sorted(by.items())}
+    out["p99_s_by_size_class"] = {names[c]: float(np.percentile(v, 99)) for c, v in sorted(by.items())}
+    arrived = [r for r in reqs if r.arrival <= out["wall_s"]]
+    out["arrived_within_limit"] = len(arrived)
+    out["offered_within_limit_amp_updates_per_s"] = sum(r.amp_updates for r in arrived) / out["wall_s"]
+    out["config"] = {"requests": count, "rate_per_s": rate, "budget_gb": budget_gb, "pool_gb": pool_gb,
+                     "time_limit_s": time_limit, "block_log2": 10, "threads_per_cta": 128, "max_batch": 64,
+                     "graphs": True, "admission": "estimated compressed footprint (learned per class) and "
+                                                   "actual pool usage under the budget"}
     out["clocks"] = clk.summary()
     srv.close()
     return out
+
+
+def run_serving(args):
+    """The serving stream on its own (2000 requests at 20/s by default) for --serve-seconds."""
+    return serving_run(args.serve_count, args.serve_rate, args.serve_seconds, args.pool_gb or 150.0,
+                       args.serve_budget_gb)
 
 
 def main():
@@ -762,6 +798,10 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=20.0)
     ap.add_argument("--serve-seconds", type=float, default=90.0)
     ap.add_argument("--serve-budget-gb", type=float, default=120.0)
+    ap.add_argument("--serve-in-bench", type=int, default=100,
+                    help="requests of the serving stream run after the timed passes (0: none)")
+    ap.add_argument("--serve-in-bench-limit", type=float, default=120.0,
+                    help="wall-time limit of that serving run (unfinished requests are censored)")
     args = ap.parse_args()
     if args.full_circuit:
         print(json.dumps(run_full_circuit(args)))

@@ -74,6 +74,9 @@ typedef struct {
                                 provably reproduced their codes (or a partner block's), so
                                 the stream is what recoding would have written */
   uint64_t replayed_passes;  /* passes re-run after an arena overflow, since creation */
+  uint64_t peak_compressed_bytes; /* largest compressed_bytes of any pass since the last
+                                     sv_reset_basis: the paper's minimum compression ratio over
+                                     a run (Sec. III) is the raw size divided by this */
 } sv_stats_t;
 
 /* ---------------------------------------------------------------------------------------
@@ -115,7 +118,12 @@ int sv_reset_basis(sv_state* s, uint64_t index);
  * Normalize(S) (global scale 1/sqrt(N) of the stored norm N), GateComputation(G, S),
  * Compress(S). Slices are processed in every pass, also where the controls make the gate
  * the identity. Targets at or above block_log2 pair the 2^h coupled blocks inside one CTA
- * (h <= 2: SV_ERR_UNSUPPORTED otherwise). k in 1..3 targets.
+ * (h <= 2: SV_ERR_UNSUPPORTED otherwise). k in 1..5 targets (Sec. II applies any gate; the
+ * paper does not bound k): G is a dense 2^k x 2^k complex matrix, e.g. several gates fused
+ * into one; with k >= 4 the CTA also keeps the matrix in fixed point, and 4096-amplitude
+ * blocks (block_log2 12) with two high targets then exceed the shared memory of a CTA
+ * (SV_ERR_UNSUPPORTED). SV_ERR_ARG: k outside 1..5, a qubit outside 0..n-1, repeated or
+ * shared between targets and controls.
  * Plain path: G applied in place to the uncompressed vector (no normalization).
  * Asynchronous; errors raised on the device are reported by the next synchronizing call.
  * ------------------------------------------------------------------------------------- */
@@ -129,8 +137,9 @@ int sv_apply_gate(sv_state* s, const double* G, const int* targets, int k,
  *   is pinned memory; all work goes to `stream`, which every state of a step must use.
  * sv_batch_apply: gates[i] to states[i] for i < count: each state gets one Algorithm 1 pass
  *   exactly as sv_apply_gate would give it (bit-identical results). States must be compressed,
- *   of one dtype and one block size, each at most once per call. Asynchronous; each state's
- *   errors and overflow replay are handled by its own sv_sync.
+ *   of one dtype and one block size, each at most once per call; gates of at most 3 qubits
+ *   (SV_ERR_UNSUPPORTED for 4 and 5). Asynchronous; each state's errors and overflow replay
+ *   are handled by its own sv_sync.
  * sv_batch_use_graphs: capture the step (descriptor copy, pass, norm kernels) as CUDA graphs,
  *   one per batch shape (count, gate width, coupled blocks, groups) and replay them.
  * ------------------------------------------------------------------------------------- */
@@ -231,7 +240,7 @@ int sv_block_stream(sv_state* s, uint64_t b, uint8_t* out, size_t cap, size_t* l
  *   `values`. SV_ERR_CORRUPT when a stream fails the bounds checks.
  * Both synchronize `stream`. The scratch they need (a few counters) is the caller's
  *   `scratch` device buffer of at least sv_codec_scratch_bytes() bytes. nblocks == 0 is a
- *   no-op that returns SV_OK (compress: *used = 0).
+ *   no-op that returns SV_OK (compress: *used = 0); the buffers may then be NULL.
  * ------------------------------------------------------------------------------------- */
 size_t sv_codec_scratch_bytes(void);
 int sv_codec_compress(const void* values, uint64_t nblocks, int block_log2, int dtype,
@@ -264,7 +273,7 @@ int sv_codec_decompress(const void* in, const uint64_t* offsets, const uint32_t*
  * its results back and synchronizes `stream`, so it cannot be recorded into a CUDA graph: on a
  * stream that is capturing (or whose capture state cannot be read) it returns SV_ERR_ARG
  * before enqueueing anything. nblocks == 0: SV_OK with *used = 0 and *norm = 0, nothing
- * launched. No memory is allocated.
+ * launched (the buffers may then be NULL). No memory is allocated.
  * ------------------------------------------------------------------------------------- */
 #define SV_STATIC_MAX_BLOCKS 65536
 int sv_codec_compress_static(const void* values, uint64_t nblocks, int block_log2, int dtype,

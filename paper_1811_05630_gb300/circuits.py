@@ -122,6 +122,88 @@ def random_brickwork(n: int, depth: int, seed: int) -> List[Gate]:
     return gates
 
 
+def expand(matrix: np.ndarray, targets: Sequence[int], controls: Sequence[int], qubits: Sequence[int]) -> np.ndarray:
+    """The gate (matrix on `targets`, applied where every control is 1) as a dense matrix on
+    `qubits` (a superset of targets and controls; qubits[0] is the least significant bit of
+    the result's basis index)."""
+    k = len(qubits)
+    pos = {q: i for i, q in enumerate(qubits)}
+    tb = [pos[t] for t in targets]
+    cmask = sum(1 << pos[c] for c in controls)
+    tmask = sum(1 << b for b in tb)
+    M = np.zeros((1 << k, 1 << k), dtype=np.complex128)
+    for x in range(1 << k):
+        if (x & cmask) != cmask:
+            M[x, x] = 1.0
+            continue
+        xt = sum(((x >> b) & 1) << i for i, b in enumerate(tb))
+        rest = x & ~tmask
+        for yt in range(1 << len(tb)):
+            y = rest | sum(((yt >> i) & 1) << b for i, b in enumerate(tb))
+            M[y, x] = matrix[yt, xt]
+    return M
+
+
+def fuse(gates: Sequence[Gate], max_qubits: int = 5, block_log2: int | None = None,
+         max_high: int = 2) -> List[Gate]:
+    """Gate fusion: consecutive gates merged into dense unitaries on at most `max_qubits`
+    qubits (with at most `max_high` of them at or above `block_log2`, the number of coupled
+    blocks a pass can hold). A gate joins the latest group it shares a qubit with when the union
+    fits, else a later group (it commutes with every group after the last one it shares a qubit
+    with), else it starts a group. A group of one gate is emitted unchanged; others become one
+    gate on the sorted union of their qubits, named FUSED<count>, with the matrix product
+    computed here once in FP64 (the simulators consume the resulting matrices as given)."""
+    groups: List[dict] = []
+
+    def high(qs):
+        return 0 if block_log2 is None else sum(1 for q in qs if q >= block_log2)
+
+    for g in gates:
+        Q = set(g.targets) | set(g.controls)
+        last = -1
+        for i in range(len(groups) - 1, -1, -1):
+            if groups[i]["qubits"] & Q:
+                last = i
+                break
+        choice = -1
+        for i in [last] + list(range(len(groups) - 1, last, -1)) if last >= 0 else range(len(groups) - 1, -1, -1):
+            u = groups[i]["qubits"] | Q
+            if len(u) <= max_qubits and high(u) <= max_high:
+                choice = i
+                break
+        if choice < 0:
+            groups.append({"qubits": set(Q), "gates": [g]})
+        else:
+            groups[choice]["qubits"] |= Q
+            groups[choice]["gates"].append(g)
+    out: List[Gate] = []
+    for grp in groups:
+        if len(grp["gates"]) == 1:
+            out.append(grp["gates"][0])
+            continue
+        qs = sorted(grp["qubits"])
+        U = np.eye(1 << len(qs), dtype=np.complex128)
+        for g in grp["gates"]:
+            U = expand(g.matrix, g.targets, g.controls, qs) @ U
+        out.append(Gate(U, tuple(qs), (), "FUSED%d" % len(grp["gates"])))
+    return out
+
+
+def unfused_count(gates: Sequence[Gate]) -> int:
+    """Gates of the original circuit a (possibly fused) gate list stands for."""
+    return sum(int(g.name[5:]) if g.name.startswith("FUSED") else 1 for g in gates)
+
+
+def haar_unitary(k: int, rng: np.random.Generator) -> np.ndarray:
+    """A Haar-random 2^k x 2^k unitary: QR of a complex Gaussian matrix with the phases of R's
+    diagonal moved into Q."""
+    d = 1 << k
+    z = (rng.standard_normal((d, d)) + 1j * rng.standard_normal((d, d))) / math.sqrt(2.0)
+    q, r = np.linalg.qr(z)
+    ph = np.diag(r) / np.abs(np.diag(r))
+    return np.ascontiguousarray(q * ph[None, :])
+
+
 def count_amplitude_updates(n: int, gates: Sequence[Gate]) -> int:
     """Amplitude-updates of a circuit: 2^n per (unfused) gate."""
     return (1 << n) * len(gates)

@@ -103,6 +103,11 @@ struct sv_state {
   // plain
   Region psi_r;
   void* psi = nullptr;
+  // device copy of the current 4- or 5-qubit gate matrix (FP64, then its FP32 rounding),
+  // written on the state's stream before each pass that uses it
+  Region gate_r;  // plain states (compressed states keep it in their metadata run)
+  double* gslot = nullptr;
+  float* gslotf = nullptr;
   // compressed
   unsigned long long nblocks = 0;
   Region meta_r, arena_r[2], aux_r;
@@ -176,7 +181,7 @@ int status_to_err(unsigned int st) {
 }
 
 bool gate_args_ok(const sv_state* s, const int* targets, int k, const int* controls, int nc) {
-  if (!targets || k < 1 || k > 3 || nc < 0 || (nc > 0 && !controls)) return false;
+  if (!targets || k < 1 || k > 5 || nc < 0 || (nc > 0 && !controls)) return false;
   unsigned long long seen = 0;
   for (int l = 0; l < k; ++l) {
     if (targets[l] < 0 || targets[l] >= s->n || ((seen >> targets[l]) & 1ull)) return false;
@@ -263,16 +268,20 @@ void build_args(const sv_state* s, const Logged& lg, PassArgs& a) {
     unsigned long long cm = 0;
     for (int c : lg.controls) cm |= 1ull << c;
     a.cmask = cm;
-    for (int e = 0; e < 2 * a.K * a.K; ++e) {
-      a.g[e] = lg.G[e];
-      a.gf[e] = (float)lg.G[e];
+    if (a.K <= 8) {
+      for (int e = 0; e < 2 * a.K * a.K; ++e) {
+        a.g[e] = lg.G[e];
+        a.gf[e] = (float)lg.G[e];
+      }
     }
+    a.gbig = s->gslot;
+    a.gfbig = s->gslotf;
     // stream pass-through map: slot g keeps the codes of slot src when every row of the
     // members in g is a unit row (exactly 1) whose column is the same in-block position in
     // slot src; with in-block controls only src = g (the identity) qualifies
     a.cmask_high = cm & ~((1ull << s->b) - 1ull);
     const bool low_ctrl = (cm & ((1ull << s->b) - 1ull)) != 0;
-    int mslot[8], moff[8];
+    int mslot[32], moff[32];
     for (int m = 0; m < a.K; ++m) {
       mslot[m] = a.pos_delta[m] / a.nv;
       moff[m] = a.pos_delta[m] % a.nv;
@@ -301,11 +310,29 @@ void build_args(const sv_state* s, const Logged& lg, PassArgs& a) {
   a.ngroups = s->nblocks >> a.h;
 }
 
+constexpr size_t kGateSlot = (size_t)2 * 32 * 32 * (sizeof(double) + sizeof(float));
+
+// Copy a 4- or 5-qubit gate matrix to the state's device slot on its stream (the pass that
+// reads it is launched after it on the same stream; the next copy waits for that pass).
+cudaError_t upload_gate(const sv_state* s, const double* G, int K) {
+  const size_t n = (size_t)2 * K * K;
+  std::vector<float> gf(n);
+  for (size_t e = 0; e < n; ++e) gf[e] = (float)G[e];
+  // pageable sources: the calls return once the bytes are staged, so the buffers may go
+  cudaError_t e = cudaMemcpyAsync(s->gslot, G, n * sizeof(double), cudaMemcpyHostToDevice, s->st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(s->gslotf, gf.data(), n * sizeof(float), cudaMemcpyHostToDevice, s->st);
+  return e;
+}
+
 // Launch pass + norm tree + finalize for one logged step of one state.
 int launch_logged(sv_state* s, const Logged& lg) {
   if (!s->arena[lg.in_id] || !s->arena[lg.out_id]) return SV_ERR_OOM;  // lost to a failed regrowth
   PassArgs a;
   build_args(s, lg, a);
+  if (!lg.basis && a.K > 8) {
+    const cudaError_t ge = upload_gate(s, lg.G.data(), a.K);
+    if (ge != cudaSuccess) return cuda_err(ge);
+  }
   std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
   if (s->timing && !lg.basis) {
     if (s->ev_free.empty()) {
@@ -492,6 +519,13 @@ int sv_create_ex(sv_pool* pool, int n, int sl, int bl, double eb, int dtype, siz
       return SV_ERR_OOM;
     }
     s->psi = pool_ptr(pool, s->psi_r.off);
+    if (!region_alloc(pool, &s->gate_r, kGateSlot)) {
+      region_free(pool, &s->psi_r);
+      delete s;
+      return SV_ERR_OOM;
+    }
+    s->gslot = (double*)pool_ptr(pool, s->gate_r.off);
+    s->gslotf = (float*)(s->gslot + 2 * 32 * 32);
     pool->nstates++;
     int rc = cuda_err(launch_plain_basis(s->psi, n, dtype == SV_C64 ? 1 : 2, 0, s->st));
     *out = s;
@@ -530,6 +564,8 @@ int sv_create_ex(sv_pool* pool, int n, int sl, int bl, double eb, int dtype, siz
   off += round_up(nb * 8, 256);
   const size_t o_tree = off;
   off += round_up(2 * (nb / 256 + 1) * 8, 256);
+  const size_t o_gate = off;
+  off += round_up(kGateSlot, 256);
   if (!region_alloc(pool, &s->meta_r, off)) {
     delete s;
     return SV_ERR_OOM;
@@ -548,6 +584,8 @@ int sv_create_ex(sv_pool* pool, int n, int sl, int bl, double eb, int dtype, siz
   s->binfo[1] = (BlkInfo*)(m + o_info1);
   s->vsum = (double*)(m + o_vsum);
   s->tree = (double*)(m + o_tree);
+  s->gslot = (double*)(m + o_gate);
+  s->gslotf = (float*)(s->gslot + 2 * 32 * 32);
   // arenas: the initial state is nearly all 16-byte CONST blocks
   const size_t init_cap = arena_bytes ? arena_bytes : std::max<size_t>(kPage, nb * 64);
   s->fixed_arena = arena_bytes != 0;
@@ -583,6 +621,7 @@ int sv_destroy(sv_state* s) {
   }
   if (s->hsc) cudaFreeHost(s->hsc);
   region_free(s->pool, &s->psi_r);
+  region_free(s->pool, &s->gate_r);
   region_free(s->pool, &s->meta_r);
   region_free(s->pool, &s->arena_r[0]);
   region_free(s->pool, &s->arena_r[1]);
@@ -617,11 +656,20 @@ int sv_apply_gate(sv_state* s, const double* G, const int* targets, int k, const
   if (s->plain) {
     unsigned long long cm = 0;
     for (int l = 0; l < nc; ++l) cm |= 1ull << controls[l];
-    return cuda_err(launch_plain_gate(s->psi, s->n, s->dtype == SV_C64 ? 1 : 2, G, targets, k, cm, s->st));
+    if (k > 3) {
+      const cudaError_t ge = upload_gate(s, G, 1 << k);
+      if (ge != cudaSuccess) return cuda_err(ge);
+    }
+    return cuda_err(launch_plain_gate(s->psi, s->n, s->dtype == SV_C64 ? 1 : 2, G, targets, k, cm,
+                                      s->gslot, s->st));
   }
   int nh = 0;
   for (int l = 0; l < k; ++l) nh += targets[l] >= s->b;
   if (nh > 2) return SV_ERR_UNSUPPORTED;
+  // the CTA's shared memory must hold the group's blocks and, for 4- and 5-qubit gates, the
+  // fixed-point matrix (4096-amplitude blocks with two high targets do not fit)
+  if (make_layout(s->b, 1 << nh, s->dtype == SV_C64 ? 4 : 8, false, k > 3).total > 227u * 1024u)
+    return SV_ERR_UNSUPPORTED;
   Logged lg;
   lg.G.assign(G, G + 2 * (1 << k) * (1 << k));
   lg.targets.assign(targets, targets + k);
@@ -753,6 +801,7 @@ int sv_stats(sv_state* s, sv_stats_t* out) {
   std::memset(out, 0, sizeof(*out));
   if (s->plain) {
     out->compressed_bytes = (uint64_t)(s->dtype == SV_C64 ? 8 : 16) << s->n;
+    out->peak_compressed_bytes = out->compressed_bytes;
     return SV_OK;
   }
   DevScalars h;
@@ -771,6 +820,7 @@ int sv_stats(sv_state* s, sv_stats_t* out) {
   out->sigma = h.sigma;
   out->blocks_reused = h.last.reused;
   out->replayed_passes = s->replayed;
+  out->peak_compressed_bytes = h.peak_bytes;
   return SV_OK;
 }
 
@@ -1042,7 +1092,7 @@ int sv_batch_apply(sv_batch* bt, sv_state* const* states, const sv_gate_t* gates
       if (states[j] == s) return SV_ERR_ARG;  // one gate per state per step
     int nh = 0;
     for (int l = 0; l < g.k; ++l) nh += g.targets[l] >= s->b;
-    if (nh > 2) return SV_ERR_UNSUPPORTED;
+    if (nh > 2 || g.k > 3) return SV_ERR_UNSUPPORTED;  // batches: gates of at most 3 qubits
     if (!s->arena[0] || !s->arena[1]) return SV_ERR_OOM;  // lost to a failed regrowth
   }
   // stage descriptors and tables in the next pinned buffer of the ring
@@ -1147,14 +1197,14 @@ size_t sv_codec_scratch_bytes(void) { return round_up(sizeof(DevScalars), 256); 
 int sv_codec_compress(const void* values, uint64_t nblocks, int bl, int dtype, double eb, void* out,
                       uint64_t cap, uint64_t* offsets, uint32_t* lengths, void* scratch,
                       void* stream, uint64_t* used) {
-  if (!values || !out || !offsets || !lengths || !scratch || bl < 5 || bl > 12 ||
-      (dtype != SV_C64 && dtype != SV_C128) || !(eb > 0.0) || !std::isfinite(eb) ||
-      ((uintptr_t)out & 15) || ((uintptr_t)scratch & 15))
+  if (bl < 5 || bl > 12 || (dtype != SV_C64 && dtype != SV_C128) || !(eb > 0.0) || !std::isfinite(eb))
     return SV_ERR_ARG;
-  if (nblocks == 0) {  // nothing to compress
+  if (nblocks == 0) {  // nothing to compress (the buffers may be NULL)
     if (used) *used = 0;
     return SV_OK;
   }
+  if (!values || !out || !offsets || !lengths || !scratch || ((uintptr_t)out & 15) || ((uintptr_t)scratch & 15))
+    return SV_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   DevScalars* sc = (DevScalars*)scratch;
   QuantP qp;
@@ -1177,11 +1227,11 @@ int sv_codec_compress(const void* values, uint64_t nblocks, int bl, int dtype, d
 int sv_codec_decompress(const void* in, const uint64_t* offsets, const uint32_t* lengths,
                         uint64_t nblocks, int bl, int dtype, double eb, void* values, void* scratch,
                         void* stream) {
-  if (!in || !offsets || !lengths || !values || !scratch || bl < 5 || bl > 12 ||
-      (dtype != SV_C64 && dtype != SV_C128) || !(eb > 0.0) || !std::isfinite(eb) ||
-      ((uintptr_t)in & 15) || ((uintptr_t)scratch & 15))
+  if (bl < 5 || bl > 12 || (dtype != SV_C64 && dtype != SV_C128) || !(eb > 0.0) || !std::isfinite(eb))
     return SV_ERR_ARG;
-  if (nblocks == 0) return SV_OK;  // nothing to decode
+  if (nblocks == 0) return SV_OK;  // nothing to decode (the buffers may be NULL)
+  if (!in || !offsets || !lengths || !values || !scratch || ((uintptr_t)in & 15) || ((uintptr_t)scratch & 15))
+    return SV_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   DevScalars* sc = (DevScalars*)scratch;
   QuantP qp;

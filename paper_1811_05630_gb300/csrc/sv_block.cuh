@@ -60,14 +60,18 @@ struct __align__(16) PassArgs {
   int low_t[5];       // low targets ascending (for base enumeration)
   int high_pos[5];    // (high target - b) ascending (block-id expansion)
   int slot_shift[5];  // for slot bit l (target order of high targets): block-id bit
-  int pos_delta[8];   // value-position offset of tuple member m within the group
+  int pos_delta[32];  // value-position offset of tuple member m within the group
   unsigned long long cmask;
   int apply_gate;     // 0: identity (initial compression)
   int input_basis;    // 1: the input is the basis state |basis>
   unsigned long long basis;
   int use_sigma;
-  double g[2 * 64];   // gate matrix (re, im), row-major K x K
+  double g[2 * 64];   // gate matrix (re, im), row-major K x K, for K <= 8
   float gf[2 * 64];
+  // K = 16 or 32 (4- and 5-qubit gates): the matrix in device memory (the state's gate slot,
+  // written on the state's stream before the launch), FP64 and its FP32 rounding
+  const double* gbig;
+  const float* gfbig;
   QuantP qp;
   double two2;
   double two_r;       // fl(2eb * r), the dequantize-requantize factor (about 1)
@@ -116,6 +120,21 @@ struct FastGate {
   int32_t idhi, idlo; // the identity scaled by sigma (members whose controls are not all 1)
 };
 
+// Fixed-point form of a 4- or 5-qubit gate (K = 16 or 32 members per tuple) for complex128,
+// prepared by all threads of a CTA: the same quantities as FastGate, with the coefficient
+// tables transposed (entry ((m * 2 + c) * 2 + p) * K + jj) so that the lanes of a warp, which
+// take consecutive output rows jj of one tuple, read consecutive words. complex64 keeps the
+// FP32 matrix in the chi area instead (entry 2 (m K + jj) + {0: re, 1: im}).
+struct BigGate {
+  int F, diag, real, qsafe;
+  long long margin;
+  int32_t idhi, idlo;
+  double rows[32];  // row sums of |c| (scratch of the preparation)
+  int8_t ssrc[32][2], ssgn[32][2];
+  int32_t chi[4 * 32 * 32];
+  int32_t clo[4 * 32 * 32];
+};
+
 // Dynamic shared-memory layout of a worker CTA (host and device agree on it).
 struct Layout {
   int nv, G, hs, dcap, p2cap;
@@ -134,7 +153,8 @@ __host__ __device__ inline int next_pow2(int x) {
 }
 
 // `batch`: the batched pass also keeps the current state's descriptor in shared memory.
-__host__ __device__ inline Layout make_layout(int b, int G, int csize, bool batch = false) {
+// `big`: the pass applies 4- or 5-qubit gates (the fixed-point area holds a BigGate).
+__host__ __device__ inline Layout make_layout(int b, int G, int csize, bool batch = false, bool big = false) {
   Layout L;
   L.nv = 2 << b;
   L.G = G;
@@ -179,7 +199,7 @@ __host__ __device__ inline Layout make_layout(int b, int G, int csize, bool batc
   L.off_misc = o;
   o += (uint32_t)pad_to(sizeof(Misc), 16);  // scalars and scan workspace
   L.off_fast = o;
-  o += (uint32_t)pad_to(sizeof(FastGate), 16);
+  o += (uint32_t)pad_to(big ? sizeof(BigGate) : sizeof(FastGate), 16);
   L.off_desc = o;  // the batched pass keeps the current state's descriptor here
   if (batch) o += (uint32_t)pad_to(sizeof(PassArgs), 16);
   L.off_vmask = o;  // complex64: one bit per value marks a verbatim value kept in place

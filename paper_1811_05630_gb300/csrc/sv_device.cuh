@@ -52,6 +52,7 @@ struct DevScalars {
   unsigned long long last_bytes;
   unsigned long long pass_index;
   unsigned long long io_bytes;   // compressed bytes read + written, summed over passes
+  unsigned long long peak_bytes; // largest stored state (compressed bytes) since the reset
   double sigma;                // scale for the next pass, 1/sqrt(norm)
   double norm;                 // N of the current stored state
   unsigned int status;

@@ -63,8 +63,9 @@ cudaError_t launch_qft_overlap_chunk(const double* amp, unsigned long long start
                                      unsigned long long x, int n, double* acc, cudaStream_t st);
 
 // Plain (uncompressed) path.
+// G: host matrix (k <= 3) ; G_dev: the same matrix in device memory (read for k = 4, 5)
 cudaError_t launch_plain_gate(void* psi, int n, int dtype, const double* G, const int* targets,
-                              int k, unsigned long long cmask, cudaStream_t st);
+                              int k, unsigned long long cmask, const double* G_dev, cudaStream_t st);
 cudaError_t launch_plain_basis(void* psi, int n, int dtype, unsigned long long index,
                                cudaStream_t st);
 cudaError_t launch_plain_read(const void* psi, int dtype, unsigned long long start,

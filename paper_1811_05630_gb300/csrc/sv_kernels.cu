@@ -33,6 +33,7 @@ __device__ void finalize_state(DevScalars* sc, double V, double two2, int reset_
   sc->last.reused = __ldcg(&sc->acc.reused);
   const unsigned long long used_out = __ldcg(&sc->bump[reset_id ^ 1]), used_in = __ldcg(&sc->bump[reset_id]);
   sc->last_bytes = used_out;
+  if (used_out > sc->peak_bytes) sc->peak_bytes = used_out;
   sc->io_bytes += used_in + used_out;
   sc->acc.sq_lo = sc->acc.sq_hi = 0;
   sc->acc.n_verbatim = sc->acc.n_escape = 0;
@@ -592,8 +593,51 @@ __global__ void k_plain_gate(Real* psi, const PlainGate pg) {
   }
 }
 
+// 4- and 5-qubit gates (K = 16 or 32) on the plain vector: K lanes of a warp own the K
+// members of one tuple; each lane loads its member, the members are exchanged by shuffles (so
+// every input is read before any lane writes), and lane j computes output row j from the matrix
+// kept in shared memory in transposed order (lanes read consecutive entries).
+template <typename Real>
+__global__ void __launch_bounds__(256) k_plain_gate_big(Real* psi, const PlainGate pg, const double* __restrict__ G) {
+  __shared__ Real gs[2 * 32 * 32];
+  const int K = pg.K;
+  for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
+    const int j = e / K, m = e % K;
+    gs[2 * (m * K + j)] = (Real)G[2 * e];
+    gs[2 * (m * K + j) + 1] = (Real)G[2 * e + 1];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, j = lane % K, lead = lane - j;
+  const int tpw = 32 / K;
+  const unsigned long long ntup = 1ull << (pg.n - pg.nfix);
+  const unsigned long long warp = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
+  const unsigned long long nwarps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+  for (unsigned long long u0 = warp * tpw; u0 < ntup; u0 += nwarps * tpw) {
+    const unsigned long long u = u0 + (unsigned long long)(lane / K);
+    const bool valid = u < ntup;
+    unsigned long long i = 0;
+    Real yr = 0, yi = 0;
+    if (valid) {
+      i = plain_base(u, pg) + pg.delta[j];
+      yr = psi[2 * i];
+      yi = psi[2 * i + 1];
+    }
+    Real ar = 0, ai = 0;
+    for (int m = 0; m < K; ++m) {
+      const Real xr = __shfl_sync(0xffffffffu, yr, lead + m), xi = __shfl_sync(0xffffffffu, yi, lead + m);
+      const Real gr = gs[2 * (m * K + j)], gi = gs[2 * (m * K + j) + 1];
+      ar = pfma<Real>(gr, xr, pfma<Real>(-gi, xi, ar));
+      ai = pfma<Real>(gr, xi, pfma<Real>(gi, xr, ai));
+    }
+    if (valid) {
+      psi[2 * i] = ar;
+      psi[2 * i + 1] = ai;
+    }
+  }
+}
+
 cudaError_t launch_plain_gate(void* psi, int n, int dtype, const double* G, const int* targets,
-                              int k, unsigned long long cmask, cudaStream_t st) {
+                              int k, unsigned long long cmask, const double* G_dev, cudaStream_t st) {
   PlainGate pg;
   memset(&pg, 0, sizeof(pg));
   pg.k = k;
@@ -609,6 +653,16 @@ cudaError_t launch_plain_gate(void* psi, int n, int dtype, const double* G, cons
     for (int l = 0; l < k; ++l)
       if ((mm >> l) & 1) d |= 1ull << targets[l];
     pg.delta[mm] = d;
+  }
+  if (k > 3) {  // the matrix is read from G_dev
+    const unsigned long long ntup = 1ull << (n - pg.nfix);
+    const unsigned long long warps = (ntup * pg.K + 31) / 32;
+    unsigned long long blocks = (warps + 7) / 8;
+    if (blocks > 152ull * 8) blocks = 152ull * 8;
+    if (blocks == 0) blocks = 1;
+    if (dtype == 1) k_plain_gate_big<float><<<(unsigned int)blocks, 256, 0, st>>>((float*)psi, pg, G_dev);
+    else k_plain_gate_big<double><<<(unsigned int)blocks, 256, 0, st>>>((double*)psi, pg, G_dev);
+    return cudaGetLastError();
   }
   for (int e = 0; e < 2 * pg.K * pg.K; ++e) pg.g[e] = G[e];
   // classify: diagonal, permutation (unit rows with coefficient exactly 1), or dense

@@ -231,11 +231,23 @@ __device__ __forceinline__ void tuple_exact(Worker<Real>& w, const PassArgs& a, 
 // ---------------------------------------------------------------------------------------
 // One group of 2^h coupled blocks of one state: Decompress, Normalize + GateComputation,
 // Compress (shared by the single-state and the batched pass kernels).
+#include "sv_pass_big.cuh"
+
+// fgv: the CTA's FastGate (KM <= 8) or BigGate (KM = 32), prepared before the first group
 template <typename Real, int KM>
-__device__ __forceinline__ void pass_group(Worker<Real>& w, const PassArgs& a, const FastGate* __restrict__ fg,
+__device__ __forceinline__ void pass_group(Worker<Real>& w, const PassArgs& a, const void* __restrict__ fgv,
                                            double sigma, unsigned long long grp) {
   using A = Arith<Real>;
   const Layout& L = w.L;
+  const FastGate* __restrict__ fg = (const FastGate*)fgv;
+  int fF, fqsafe;  // fixed-point form available (F >= 0) and the single-term code limit
+  if constexpr (KM > 8) {
+    fF = ((const BigGate*)fgv)->F;
+    fqsafe = ((const BigGate*)fgv)->qsafe;
+  } else {
+    fF = fg->F;
+    fqsafe = fg->qsafe;
+  }
   const Real sg = (Real)sigma;  // complex64: sigma rounded to float once
   const int B = L.nv / 2;
   constexpr bool kFast = sizeof(Real) == 8;
@@ -271,7 +283,7 @@ __device__ __forceinline__ void pass_group(Worker<Real>& w, const PassArgs& a, c
   if (a.pt_ok) {
     if (threadIdx.x == 0) {
       const bool hc = ((blks[0] << a.b) & a.cmask_high) == a.cmask_high;
-      const bool unit_rule = kFast && (a.pt_ok & 2) && fg->F >= 0;
+      const bool unit_rule = kFast && (a.pt_ok & 2) && fF >= 0;
       unsigned int dmask = 0;
       int npt = 0;
       for (int g = 0; g < a.G; ++g) {
@@ -281,7 +293,7 @@ __device__ __forceinline__ void pass_group(Worker<Real>& w, const PassArgs& a, c
           const int c = hc ? a.pt_src[g] : g;
           if (c >= 0) {
             const unsigned int mm = a.in_info[blks[c]].maxq_mode;
-            if (!(mm & 0x80000000u) && (long long)(mm & 0x1FFFFFFFu) <= (long long)fg->qsafe) src = c;
+            if (!(mm & 0x80000000u) && (long long)(mm & 0x1FFFFFFFu) <= (long long)fqsafe) src = c;
           }
         }
         if (src < 0) {
@@ -329,6 +341,11 @@ __device__ __forceinline__ void pass_group(Worker<Real>& w, const PassArgs& a, c
       }
     }
     // ---- Normalize(S) and GateComputation(G, S), tuple by tuple, in place ----
+    if constexpr (KM > 8) {
+      __syncthreads();  // every block of the group is decoded
+      big_gate_stage<Real>(w, a, (const BigGate*)fgv, sigma, blks[0]);
+    }
+    if constexpr (KM <= 8) {
     const int ntup = B >> a.nlow;
     for (int u = threadIdx.x; u < ntup; u += blockDim.x) {
       unsigned long long o = (unsigned long long)u;
@@ -431,6 +448,7 @@ __device__ __forceinline__ void pass_group(Worker<Real>& w, const PassArgs& a, c
       }
       tuple_exact<Real, KM>(w, a, sg, bp, ctrl);
     }
+    }
     __syncthreads();
     if (round == 0) {
       // ---- Compress(S) ----
@@ -454,7 +472,7 @@ __device__ __forceinline__ void pass_group(Worker<Real>& w, const PassArgs& a, c
 template <typename Real, int KM>
 __device__ __forceinline__ void pass_body(const PassArgs& a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const Layout L = make_layout(a.b, a.G, (int)sizeof(Real));
+  const Layout L = make_layout(a.b, a.G, (int)sizeof(Real), false, KM > 8);
   Worker<Real> w;
   w.init(smem, L, a.b, a.qp);
   if (a.chunk) w.kc = a.chunk;
@@ -467,8 +485,12 @@ __device__ __forceinline__ void pass_body(const PassArgs& a) {
   __syncthreads();
   if (w.m->live) {
     const double sigma = a.use_sigma ? *(volatile double*)&a.sc->sigma : 1.0;
-    FastGate* fg = (FastGate*)(smem + L.off_fast);
-    if (sizeof(Real) == 8 && threadIdx.x == 0) fast_prepare(fg, a, sigma);  // visible after pass_group's barrier
+    void* fg = smem + L.off_fast;
+    if constexpr (KM > 8) {
+      big_prepare<Real>((BigGate*)fg, a, sigma);  // all threads; ends with a barrier
+    } else {
+      if (sizeof(Real) == 8 && threadIdx.x == 0) fast_prepare((FastGate*)fg, a, sigma);  // visible after pass_group's barrier
+    }
     for (unsigned long long grp = blockIdx.x; grp < a.ngroups; grp += gridDim.x)
       pass_group<Real, KM>(w, a, fg, sigma, grp);
     if (threadIdx.x == 0 && w.m->err) {
@@ -492,7 +514,7 @@ __global__ void __launch_bounds__(256, 4) k_pass_c(const PassArgs a) {
 
 template <typename Real, int KM, bool COMPACT>
 static cudaError_t launch_pass_k(const PassArgs& a, cudaStream_t st) {
-  const Layout L = make_layout(a.b, a.G, (int)sizeof(Real));
+  const Layout L = make_layout(a.b, a.G, (int)sizeof(Real), false, KM > 8);
   static std::atomic<unsigned long long> configured{0};  // devices set up
   cudaError_t ce = once_per_device(configured, [] {
     if constexpr (COMPACT) return cudaFuncSetAttribute(k_pass_c<Real, KM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
@@ -513,7 +535,8 @@ template <typename Real>
 static cudaError_t launch_pass_t(const PassArgs& a, cudaStream_t st) {
   if (a.K <= 2) return launch_pass_k<Real, 2, false>(a, st);
   if (a.K <= 4) return launch_pass_k<Real, 4, false>(a, st);
-  return launch_pass_k<Real, 8, false>(a, st);
+  if (a.K <= 8) return launch_pass_k<Real, 8, false>(a, st);
+  return launch_pass_k<Real, 32, false>(a, st);  // 4- and 5-qubit gates
 }
 
 }  // namespace sv

@@ -91,10 +91,10 @@ extern "C" int sv_codec_compress_static(const void* values, uint64_t nblocks, in
                                         double eb, void* out, uint64_t cap, uint64_t* offsets,
                                         uint32_t* lengths, void* stream, uint64_t* used,
                                         double* norm) {
-  if (!values || !out || !offsets || !lengths || bl < 5 || bl > 12 ||
-      (dtype != SV_C64 && dtype != SV_C128) || !(eb > 0.0) || !std::isfinite(eb) || ((uintptr_t)out & 15))
+  if (bl < 5 || bl > 12 || (dtype != SV_C64 && dtype != SV_C128) || !(eb > 0.0) || !std::isfinite(eb))
     return SV_ERR_ARG;
   if (nblocks > kMaxBlocks) return SV_ERR_UNSUPPORTED;
+  if (nblocks && (!values || !out || !offsets || !lengths || ((uintptr_t)out & 15))) return SV_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   // the call ends with a read-back and a stream synchronization, neither of which a capturing
   // stream accepts: refuse before enqueueing anything (an error here means the stream's

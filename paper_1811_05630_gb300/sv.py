@@ -46,6 +46,7 @@ class Stats(ctypes.Structure):
         ("blocks_pack", ctypes.c_uint64), ("n_verbatim", ctypes.c_uint64),
         ("n_escape", ctypes.c_uint64), ("norm", ctypes.c_double), ("sigma", ctypes.c_double),
         ("blocks_reused", ctypes.c_uint64), ("replayed_passes", ctypes.c_uint64),
+        ("peak_compressed_bytes", ctypes.c_uint64),
     ]
 
     def as_dict(self):

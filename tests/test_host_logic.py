@@ -45,6 +45,9 @@ class FakeBackend:
             def __init__(self, nbytes, device="cuda"):
                 self.nbytes = nbytes
 
+            def usage(self):
+                return sum(backend.live.values()), self.nbytes
+
             def close(self):
                 pass
 
@@ -56,7 +59,8 @@ class FakeBackend:
                 self.applied = 0
                 self.closed = False
                 self.threads = 0
-                req = types.SimpleNamespace(n=n, dtype=dtype)
+                # the fake state holds what admission reserved for a request of its class
+                req = types.SimpleNamespace(n=n, dtype=dtype, eb=eb)
                 fp = serve.footprint(req, block_log2)
                 backend.live[id(self)] = fp
                 backend.peak = max(backend.peak, sum(backend.live.values()))
@@ -77,6 +81,9 @@ class FakeBackend:
 
             def norm(self):
                 return 1.0
+
+            def stats(self):  # a compressed state of 1 byte per amplitude at its peak
+                return {"peak_compressed_bytes": 1 << self.n}
 
             def close(self):
                 assert not self.closed
@@ -133,7 +140,7 @@ def small_requests(count=40, seed=3):
     return out
 
 
-def run_server(monkeypatch, reqs, budget, max_batch=4, fail_eb=None, block_log2=10):
+def run_server(monkeypatch, reqs, budget, max_batch=4, fail_eb=None, block_log2=10, time_limit=30.0):
     from paper_1811_05630_gb300 import serve
 
     fb = FakeBackend(budget, block_log2, max_batch, fail_eb)
@@ -141,7 +148,7 @@ def run_server(monkeypatch, reqs, budget, max_batch=4, fail_eb=None, block_log2=
     monkeypatch.setattr(serve, "torch", fb.torch)
     srv = serve.Server(1 << 30, budget, block_log2=block_log2, max_batch=max_batch, graphs=False)
     try:
-        out = srv.run(reqs, time_limit=30.0)
+        out = srv.run(reqs, time_limit=time_limit)
     finally:
         srv.close()
     return fb, out
@@ -209,10 +216,44 @@ def test_size_classes_and_footprint(lib):
     from paper_1811_05630_gb300 import serve
 
     assert [serve.size_class(n) for n in (10, 16, 17, 22, 23, 28)] == [0, 0, 1, 1, 2, 2]
-    r = types.SimpleNamespace(n=20, dtype=2)
-    assert serve.footprint(r, 10) == (16 << 20) + 48 * 1024 + (8 << 20)
-    r = types.SimpleNamespace(n=20, dtype=1)
-    assert serve.footprint(r, 10) == (8 << 20) + 48 * 1024 + (8 << 20)
+    MB = 1 << 20
+    # metadata of 2^10 blocks (2 x 8 + 2 x 4 + 2 x 16 + 8 bytes each, plus scalars and tree
+    # scratch) fits one 2 MiB page; two arenas at twice the expected compressed state
+    assert serve.meta_bytes(20, 10) == 2 * MB
+    r = types.SimpleNamespace(n=20, dtype=2, eb=1e-6)  # prior: 8 bytes per amplitude
+    assert serve.footprint(r, 10) == 2 * MB + 2 * (2 * 8 * MB)
+    r = types.SimpleNamespace(n=20, dtype=1, eb=1e-4)  # prior: 2 bytes per amplitude
+    assert serve.footprint(r, 10) == 2 * MB + 2 * (2 * 2 * MB)
+    # far below the uncompressed vector once the class is known to compress well
+    assert serve.footprint(r, 10, bytes_per_amp=0.1) == 2 * MB + 2 * (2 * MB)
+    assert serve.footprint(types.SimpleNamespace(n=28, dtype=2, eb=1e-8), 10, 0.5) < (16 << 28) // 2
+
+
+def test_footprint_model_follows_the_largest_peak_of_a_class(lib):
+    from paper_1811_05630_gb300 import serve
+
+    m = serve.FootprintModel()
+    a = C.Request(0, 0.0, "qft", 20, 2, 1e-6, 0, [])
+    b = C.Request(1, 0.0, "qft", 22, 2, 1e-6, 0, [])
+    other = C.Request(2, 0.0, "random", 20, 2, 1e-6, 0, [])
+    assert m.bytes_per_amp(a) == serve.prior_bytes_per_amp(a) == 8.0
+    m.observe(a, 2 << 20)  # peak 2 bytes per amplitude
+    assert m.bytes_per_amp(b) == 2.5  # 25 % margin, shared by the class
+    m.observe(b, 1 << 22)  # a smaller peak does not lower it
+    assert m.bytes_per_amp(a) == 2.5
+    m.observe(b, 3 << 22)
+    assert m.bytes_per_amp(a) == 3.75
+    assert m.bytes_per_amp(other) == 8.0
+
+
+def test_server_counts_unfinished_requests_as_censored(lib, monkeypatch):
+    reqs = small_requests(12, seed=4)
+    # a budget below every footprint admits nothing: every arrived request is censored, and the
+    # percentiles are lower bounds (end of the run minus arrival)
+    fb, out = run_server(monkeypatch, reqs, budget=1, time_limit=0.5)
+    assert out["completed"] == 0 and out["censored"] == len(reqs)
+    assert out["latency_is_lower_bound"] and out["p99_s"] >= out["p50_s"] > 0
+    assert out["p50_s_completed"] is None
 
 
 # ---- tuner candidates ----------------------------------------------------------------------

@@ -122,3 +122,41 @@ def test_complex64_within_fp32_tolerance():
     s64 = oracle.PlainSim(n, oracle.C64, 0).run(g).state
     assert s64.dtype == np.complex64
     assert np.abs(s64.astype(np.complex128) - s128).max() < 1e-5
+
+
+# ---- gate fusion (host-side circuit transformation) ----------------------------------------
+
+def test_expand_places_controls_and_targets():
+    from paper_1811_05630_gb300 import circuits as C
+
+    # CZ as a controlled Z on (target 3, control 1) inside qubits (1, 3): diag(1, 1, 1, -1)
+    M = C.expand(C.Z, (3,), (1,), (1, 3))
+    assert np.array_equal(M, np.diag([1, 1, 1, -1]).astype(complex))
+    # X on qubit 5 embedded as the high bit of (2, 5): swaps index pairs differing in bit 1
+    M = C.expand(C.X, (5,), (), (2, 5))
+    assert np.array_equal(M, np.kron(C.X, np.eye(2)))
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_fused_circuit_equals_the_original_on_the_plain_oracle(seed):
+    from paper_1811_05630_gb300 import circuits as C
+
+    n = 10
+    gates = C.random_brickwork(n, 5, seed=seed) + C.qft(n)
+    fused = C.fuse(gates, 5, block_log2=6)
+    assert len(fused) < len(gates) / 3 and C.unfused_count(fused) == len(gates)
+    for g in fused:
+        assert g.k + len(g.controls) <= 5 and sum(1 for q in g.targets + g.controls if q >= 6) <= 2
+        U = g.matrix
+        assert np.allclose(U.conj().T @ U, np.eye(U.shape[0]), atol=1e-12)
+    a = oracle.PlainSim(n, oracle.C128, 3).run(gates).state
+    b = oracle.PlainSim(n, oracle.C128, 3).run(fused).state
+    assert np.max(np.abs(a - b)) < 1e-12
+
+
+def test_haar_unitary_is_unitary_and_seeded():
+    from paper_1811_05630_gb300 import circuits as C
+
+    U = C.haar_unitary(5, np.random.default_rng(1))
+    assert U.shape == (32, 32) and np.allclose(U.conj().T @ U, np.eye(32), atol=1e-12)
+    assert np.array_equal(U, C.haar_unitary(5, np.random.default_rng(1)))
