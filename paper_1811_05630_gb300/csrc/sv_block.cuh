@@ -237,6 +237,56 @@ __host__ __device__ inline int worker_threads(int b) {
   return t;
 }
 
+// Pairwise sum (every node fl(left + right)) of x*x over the aligned run [j0, j0 + vpt) of a
+// block's values, x the value if it is verbatim and +0 otherwise. complex64 (mask, no ranks):
+// verbatim values are flagged in `mask` with their float bits in the code slot q[j];
+// complex128 with ranks (many verbatim values): `mask` flags them and their raw values sit in
+// `sec` at their rank (prefix counts `pre`); complex128 otherwise: the (pos, bits) list.
+// Kept out of line: it runs only for blocks with verbatim values, and its stack of pending
+// subtrees stays out of the pass's registers.
+template <typename Real>
+__device__ __noinline__ double square_run(int j0, int vpt, const uint32_t* mask, const int32_t* q,
+                                          const uint16_t* pre, const uint8_t* sec, int nlist,
+                                          const uint16_t* lpos, const uint64_t* lbits) {
+  constexpr bool kMask = sizeof(Real) == 4;
+  double stk[7];
+  int lvl[7], top = 0;
+  for (int i = 0; i < vpt; ++i) {
+    const int j = j0 + i;
+    double x2 = 0.0;
+    if (kMask) {
+      if ((mask[j >> 5] >> (j & 31)) & 1u) {
+        const double x = (double)__uint_as_float((uint32_t)q[j]);
+        x2 = __dmul_rn(x, x);
+      }
+    } else if (pre) {
+      const uint32_t wd = mask[j >> 5];
+      if ((wd >> (j & 31)) & 1u) {
+        const uint32_t rank = pre[j >> 5] + (uint32_t)__popc(wd & ((1u << (j & 31)) - 1u));
+        const double x = __longlong_as_double(*(const long long*)(sec + 8 * rank));
+        x2 = __dmul_rn(x, x);
+      }
+    } else {
+      for (int e = 0; e < nlist; ++e)
+        if (lpos[e] == j) {
+          const double x = __longlong_as_double((long long)lbits[e]);
+          x2 = __dmul_rn(x, x);
+        }
+    }
+    double v = x2;
+    int l = 0;
+    while (top > 0 && lvl[top - 1] == l) {
+      v = __dadd_rn(stk[top - 1], v);
+      --top;
+      ++l;
+    }
+    stk[top] = v;
+    lvl[top] = l;
+    ++top;
+  }
+  return stk[0];
+}
+
 template <typename Real>
 struct Worker {
   Layout L;
@@ -258,7 +308,7 @@ struct Worker {
   uint32_t* vomask;
   uint16_t *vpre_in, *vpre_out;
 
-  __device__ void init(unsigned char* smem, const Layout& lay, int b_, const QuantP& p) {
+  __device__ __forceinline__ void init(unsigned char* smem, const Layout& lay, int b_, const QuantP& p) {
     L = lay;
     b = b_;
     T = blockDim.x;
@@ -289,7 +339,7 @@ struct Worker {
   // their raw values go to the vin list). The stream is first copied into the stage buffer
   // with 16-byte loads; every later read is from shared memory. Errors set m->err.
   // ------------------------------------------------------------------------------------
-  __device__ void decode(int g, const uint8_t* s, uint32_t len) {
+  __device__ __forceinline__ void decode(int g, const uint8_t* s, uint32_t len) {
     const int tid = threadIdx.x, nv = L.nv;
     int32_t* qb = q + g * nv;
     for (int i = tid; i < (nv >> 5); i += T) vmask[g * (nv >> 5) + i] = 0u;
@@ -387,16 +437,23 @@ struct Worker {
         // of length l <= kLutBits whose canonical value is e >> (kLutBits - l) (at most one l
         // matches: the code is prefix-free); entry (canonical index + 1) << 8 | length, or 0
         // when the code is longer
+        // canonical codes left-justified to kLutBits bits increase with their length and index,
+        // so the prefix e starts a code of length l exactly when lim[l-1] <= e < lim[l], with
+        // lim[l] = (first[l] + lcount[l]) << (kLutBits - l) (an empty length repeats the
+        // previous limit); the limits and the per-length bases live in registers
         const int lshort = lmax < kLutBits ? lmax : kLutBits;
+        int lim[kLutBits + 1], base[kLutBits + 1];
+#pragma unroll
+        for (int l = 1; l <= kLutBits; ++l) {
+          const int fl = l <= lshort ? m->first[l] : 0, lc = l <= lshort ? m->lcount[l] : 0;
+          lim[l] = l <= lshort ? (fl + lc) << (kLutBits - l) : 0;
+          base[l] = l <= lshort ? m->offs[l] - fl + 1 : 0;
+        }
         for (int e = tid; e < (1 << kLutBits); e += T) {
           uint32_t v = 0;
-          for (int l = 1; l <= lshort; ++l) {
-            const int c = e >> (kLutBits - l);
-            if (c >= m->first[l] && c - m->first[l] < m->lcount[l]) {
-              v = ((uint32_t)(m->offs[l] + c - m->first[l] + 1) << 8) | (uint32_t)l;
-              break;
-            }
-          }
+#pragma unroll
+          for (int l = kLutBits; l >= 1; --l)
+            if (l <= lshort && e < lim[l]) v = ((uint32_t)(base[l] + (e >> (kLutBits - l))) << 8) | (uint32_t)l;
           lut[e] = v;
         }
       }
@@ -573,7 +630,7 @@ struct Worker {
   }
 
   // Basis input: every code 0 except the value 1.0 at `pos` (given raw, as verbatim input).
-  __device__ void load_basis(int g, int pos) {
+  __device__ __forceinline__ void load_basis(int g, int pos) {
     const int tid = threadIdx.x;
     int32_t* qb = q + g * L.nv;
     for (int j = tid; j < L.nv; j += T) qb[j] = 0;
@@ -613,7 +670,7 @@ struct Worker {
     return is_verb(g, j) ? 0 : q[g * L.nv + j];
   }
 
-  __device__ Real value_at(int g, int j) const {
+  __device__ __forceinline__ Real value_at(int g, int j) const {
     const int32_t c = q[g * L.nv + j];
     if (kMask) return is_verb(g, j) ? RawBits<Real>::from((uint32_t)c) : dequant<Real>(c, qp);
     if (c != kSentinel) return dequant<Real>(c, qp);
@@ -631,7 +688,7 @@ struct Worker {
 
   // Hash slot of a symbol that the histogram inserted; L.hs (and an error flag) when it is
   // missing, which only a logic error can cause: the probe is bounded either way.
-  __device__ uint32_t find_slot(uint32_t sym) const {
+  __device__ __forceinline__ uint32_t find_slot(uint32_t sym) const {
     uint32_t h = hash_sym(sym) & (uint32_t)(L.hs - 1);
     for (int probe = 0; probe < L.hs; ++probe) {
       const uint32_t k = hkey[h];
@@ -644,7 +701,7 @@ struct Worker {
   }
 
   // Quantize one result into slot g position j (Compress(S), first step).
-  __device__ void put_value(int g, int j, Real v) {
+  __device__ __forceinline__ void put_value(int g, int j, Real v) {
     int32_t c;
     if (kMask) {
       uint32_t* w = &vmask[g * (L.nv >> 5) + (j >> 5)];
@@ -682,13 +739,13 @@ struct Worker {
   // ------------------------------------------------------------------------------------
   // Compress(S) for one block: q codes + verbatim list -> stream in the output arena.
   // ------------------------------------------------------------------------------------
-  __device__ void encode(int g, unsigned long long blk, const PassArgs& a);
+  __device__ __forceinline__ void encode(int g, unsigned long long blk, const PassArgs& a);
 
   // Re-emit the input stream of block sb as the output stream of block db: the pass has
   // been shown to reproduce sb's codes exactly at db's positions, and encoding is a function
   // of the codes alone, so the recoded stream would be these bytes. The norm partial and
   // statistics come from sb's summary, as the recode would have added them.
-  __device__ void pass_through(unsigned long long sb, unsigned long long db, const PassArgs& a) {
+  __device__ __forceinline__ void pass_through(unsigned long long sb, unsigned long long db, const PassArgs& a) {
     const int tid = threadIdx.x;
     const uint32_t len = a.in_len[sb];
     if (tid == 0) {
@@ -726,7 +783,7 @@ struct Worker {
 
   // complex128 second round: rank of every output verbatim position of block g (per-word
   // prefix counts of the output bitmap). All threads call it.
-  __device__ void prepare_out_ranks(int g) {
+  __device__ __forceinline__ void prepare_out_ranks(int g) {
     const int W = L.nv >> 5;  // <= blockDim.x
     const uint32_t pc = (int)threadIdx.x < W ? (uint32_t)__popc(vomask[g * W + threadIdx.x]) : 0u;
     uint32_t tot = 0;
@@ -739,7 +796,7 @@ struct Worker {
   // into its stream at `out`, after the zero fill of the section
   // (complex128 with many verbatim values: positions now; the section's address is kept for
   // the second transform that writes the raw values)
-  __device__ void write_verbatim_inplace(int g, uint8_t* out, uint32_t body_end, int nverb) {
+  __device__ __forceinline__ void write_verbatim_inplace(int g, uint8_t* out, uint32_t body_end, int nverb) {
     const int tid = threadIdx.x, nv = L.nv, j0 = tid * vpt;
     const uint32_t* bm = kMask ? vmask : vomask;
     const uint32_t w = bm[g * (nv >> 5) + (j0 >> 5)];
@@ -761,49 +818,16 @@ struct Worker {
   }
 
   // Pairwise sum of x*x over the block's values (x verbatim) and +0 (others), level by
-  // level: each thread reduces its aligned run of vpt values with a stack of partial sums
-  // (every node is fl(left + right)), then the runs are reduced across threads. All threads
-  // call it; the result is returned to all.
-  __device__ double verbatim_square_tree(int g) {
-    const int tid = threadIdx.x, nv = L.nv, j0 = tid * vpt;
-    double stk[7];
-    int lvl[7], top = 0;
-    for (int i = 0; i < vpt; ++i) {
-      const int j = j0 + i;
-      double x2 = 0.0;
-      if (kMask) {
-        if (is_verb(g, j)) {
-          const double x = (double)RawBits<Real>::from((uint32_t)q[g * nv + j]);
-          x2 = __dmul_rn(x, x);
-        }
-      } else if (m->vbig[g]) {
-        const int W = nv >> 5;
-        const uint32_t wd = vomask[g * W + (j >> 5)];
-        if ((wd >> (j & 31)) & 1u) {
-          const uint32_t rank = vpre_out[g * W + (j >> 5)] + (uint32_t)__popc(wd & ((1u << (j & 31)) - 1u));
-          const double x = (double)RawBits<Real>::from(*(const uint64_t*)(m->vsec_base[g] + m->vsec_valoff[g] + 8 * rank));
-          x2 = __dmul_rn(x, x);
-        }
-      } else {
-        const int n = vout_cnt[g] < kVmax ? vout_cnt[g] : kVmax;
-        for (int e = 0; e < n; ++e)
-          if (vout_pos[g * kVmax + e] == j) {
-            const double x = (double)RawBits<Real>::from(vout_bits[g * kVmax + e]);
-            x2 = __dmul_rn(x, x);
-          }
-      }
-      double v = x2;
-      int l = 0;
-      while (top > 0 && lvl[top - 1] == l) {
-        v = __dadd_rn(stk[top - 1], v);
-        --top;
-        ++l;
-      }
-      stk[top] = v;
-      lvl[top] = l;
-      ++top;
-    }
-    vtree[tid] = stk[0];
+  // level: each thread reduces its aligned run of vpt values (square_run, below), then the
+  // runs are reduced across threads. All threads call it; the result is returned to all.
+  __device__ __forceinline__ double verbatim_square_tree(int g) {
+    const int tid = threadIdx.x, nv = L.nv, W = nv >> 5;
+    const double top = square_run<Real>(tid * vpt, vpt, kMask ? vmask + g * W : vomask + g * W,
+                                        q + g * nv, (!kMask && m->vbig[g]) ? vpre_out + g * W : nullptr,
+                                        kMask ? nullptr : m->vsec_base[g] + m->vsec_valoff[g],
+                                        vout_cnt[g] < kVmax ? vout_cnt[g] : kVmax, vout_pos + g * kVmax,
+                                        vout_bits + g * kVmax);
+    vtree[tid] = top;
     __syncthreads();
     for (int cnt = T; cnt > 1; cnt >>= 1) {
       const int half = cnt >> 1;
@@ -821,38 +845,74 @@ struct Worker {
 
 // Two-queue Huffman merge over D >= 2 leaves sorted by (frequency, symbol) in keys (frequency
 // in the upper 16 bits): each step joins the two lightest queue heads, the leaf queue first on
-// equal weight. Writes parent[v] for every node but the root (node D-1+... = 2D-2). The queue
-// heads are kept in registers so that a step waits on at most the refill of what it consumed.
-__device__ inline void huffman_merge(const uint32_t* keys, int D, uint32_t* wint, uint16_t* parent) {
-  constexpr uint32_t INF = 0xFFFFFFFFu;
-  int lp = 0, ip = 0, nint = 0;
-  uint32_t cl = keys[0] >> 16;
-  uint32_t cl_next = keys[1] >> 16;
-  uint32_t ci = INF;
-  for (int mm = 0; mm < D - 1; ++mm) {
-    int pick[2];
-    uint32_t w[2];
-#pragma unroll
-    for (int t = 0; t < 2; ++t) {
-      if (cl <= ci) {
-        pick[t] = lp;
-        w[t] = cl;
-        ++lp;
-        cl = cl_next;
-        cl_next = lp + 1 < D ? (keys[lp + 1] >> 16) : INF;
-      } else {
-        pick[t] = D + ip;
-        w[t] = ci;
-        ++ip;
-        ci = ip < nint ? wint[ip] : INF;
-      }
+// equal weight. Writes wint[k] (internal node k = node D + k) and parent[v] for every node but
+// the root (2D - 2).
+//
+// All threads, in rounds rather than D - 1 serial steps. The steps consume the nodes in the
+// order of S, the merge of the leaf list with the internal-node list (leaves first on equal
+// weight), and internal node k joins S[2k] and S[2k + 1]. With m entries of S placed, the
+// internal nodes 0 .. m/2 - 1 are known, and every node not yet formed weighs at least
+// thr = S[m-1] + v0 (m odd) or 2 v0 (m even), v0 the lightest node available now. Every
+// available node of weight <= thr therefore precedes every unformed one (a leaf wins a tie;
+// a known internal node was formed earlier), so one round places all of them at once, each at
+// its merge position, and forms the internal nodes their pairs complete. thr at least doubles
+// every round, so a block (total weight < 2^16) needs at most 17 rounds. sw, sid: scratch for
+// S (weights and node ids, 2D - 2 entries each).
+__device__ inline void huffman_merge(const uint32_t* keys, int D, uint32_t* wint, uint16_t* parent,
+                                     uint32_t* sw, uint16_t* sid) {
+  const int tid = threadIdx.x, T = blockDim.x;
+  int m = 0, lp = 0, ip = 0;  // S entries placed, leaves and internal nodes consumed (uniform)
+  while (m < 2 * D - 2) {
+    const int nk = m >> 1;  // internal nodes formed
+    uint32_t v0 = 0xFFFFFFFFu;
+    if (lp < D) v0 = keys[lp] >> 16;
+    if (ip < nk && wint[ip] < v0) v0 = wint[ip];
+    const uint32_t thr = (m & 1) ? sw[m - 1] + v0 : 2u * v0;
+    // available nodes at or below thr (each list is sorted, so they are prefixes)
+    int cl = 0, ci = 0;
+    for (int t0 = 0; t0 < D - lp; t0 += T) {
+      const int t = t0 + tid;
+      cl += __syncthreads_count(t < D - lp && (keys[lp + t] >> 16) <= thr);
     }
-    const uint32_t wn = w[0] + w[1];
-    wint[nint] = wn;
-    parent[pick[0]] = (uint16_t)(D + nint);
-    parent[pick[1]] = (uint16_t)(D + nint);
-    if (ip == nint) ci = wn;  // the new node is the only one in its queue
-    ++nint;
+    for (int t0 = 0; t0 < nk - ip; t0 += T) {
+      const int t = t0 + tid;
+      ci += __syncthreads_count(t < nk - ip && wint[ip + t] <= thr);
+    }
+    // merge positions: a leaf follows the internal nodes lighter than it, an internal node
+    // follows the leaves not heavier than it
+    for (int t = tid; t < cl; t += T) {
+      const uint32_t x = keys[lp + t] >> 16;
+      int lo = ip, hi = ip + ci;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (wint[mid] < x) lo = mid + 1;
+        else hi = mid;
+      }
+      sw[m + t + (lo - ip)] = x;
+      sid[m + t + (lo - ip)] = (uint16_t)(lp + t);
+    }
+    for (int t = tid; t < ci; t += T) {
+      const uint32_t x = wint[ip + t];
+      int lo = lp, hi = lp + cl;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if ((keys[mid] >> 16) <= x) lo = mid + 1;
+        else hi = mid;
+      }
+      sw[m + t + (lo - lp)] = x;
+      sid[m + t + (lo - lp)] = (uint16_t)(D + ip + t);
+    }
+    __syncthreads();
+    const int mn = m + cl + ci;
+    for (int k = nk + tid; k < (mn >> 1); k += T) {
+      wint[k] = sw[2 * k] + sw[2 * k + 1];
+      parent[sid[2 * k]] = (uint16_t)(D + k);
+      parent[sid[2 * k + 1]] = (uint16_t)(D + k);
+    }
+    __syncthreads();
+    m = mn;
+    lp += cl;
+    ip += ci;
   }
 }
 
@@ -915,7 +975,7 @@ __device__ inline void sort_pairs(uint32_t* key, uint32_t* val, int n, int p2, u
 }
 
 template <typename Real>
-__device__ void Worker<Real>::encode(int g, unsigned long long blk, const PassArgs& a) {
+__device__ __forceinline__ void Worker<Real>::encode(int g, unsigned long long blk, const PassArgs& a) {
   const int tid = threadIdx.x, nv = L.nv;
   const int32_t* qb = q + g * nv;
   int nverb_raw, nverb;
@@ -1046,8 +1106,9 @@ __device__ void Worker<Real>::encode(int g, unsigned long long blk, const PassAr
       if (D == 1) {
         if (tid == 0) lens[0] = 1;
       } else {
-        if (tid == 0) huffman_merge(keys, D, wint, parent);
-        __syncthreads();
+        // S of the merge in the rank-sort scratch (weights) and the second parent array (ids),
+        // both idle until the depth computation
+        huffman_merge(keys, D, wint, parent, tsk, parent2);
         lens = tree_depths(D, parent, lens, parent2, lens2);
       }
       if (tid == 0) m->lmax = 0;

@@ -136,15 +136,19 @@ __device__ __forceinline__ bool fast_round(long long W, int F, long long margin,
   return true;
 }
 
-// the exact step chain for one output component of a tuple (no verbatim input)
-__device__ __forceinline__ double exact_component(const PassArgs& a, double sigma, const int32_t* qv,
+// the exact step chain for one output component of a tuple (no verbatim input). The member
+// loop is unrolled to KM with a guard so that the caller's code array stays in registers.
+template <int KM>
+__device__ __forceinline__ double exact_component(const PassArgs& a, double sigma, const int32_t (&qv)[2 * KM],
                                                   int jj, int p, bool ctrl) {
   if (!ctrl) {
     const double x = __dmul_rn((double)qv[2 * jj + p], a.qp.two);
     return a.use_sigma ? __dmul_rn(sigma, x) : x;
   }
   double ar = 0.0, ai = 0.0;
-  for (int m = 0; m < a.K; ++m) {
+#pragma unroll
+  for (int m = 0; m < KM; ++m) {
+    if (m >= a.K) break;
     double yr = __dmul_rn((double)qv[2 * m], a.qp.two), yi = __dmul_rn((double)qv[2 * m + 1], a.qp.two);
     if (a.use_sigma) {
       yr = __dmul_rn(sigma, yr);
@@ -253,13 +257,14 @@ __device__ __forceinline__ void pass_group(Worker<Real>& w, const PassArgs& a, c
   constexpr bool kFast = sizeof(Real) == 8;
   unsigned long long base = grp;
   for (int l = 0; l < a.h; ++l) base = insert_zero_bit(base, a.high_pos[l]);
-  unsigned long long blks[4];
-  for (int g = 0; g < a.G; ++g) {
+  // block id of group slot g (a function rather than an array indexed at run time, which
+  // would live in local memory)
+  auto blk_of = [&](int g) -> unsigned long long {
     unsigned long long bid = base;
     for (int l = 0; l < a.h; ++l)
       if ((g >> l) & 1) bid |= 1ull << a.slot_shift[l];
-    blks[g] = bid;
-  }
+    return bid;
+  };
   __syncthreads();
   if (threadIdx.x < 4) {
     w.vout_cnt[threadIdx.x] = 0;
@@ -282,7 +287,7 @@ __device__ __forceinline__ void pass_group(Worker<Real>& w, const PassArgs& a, c
   bool any_pt = false;
   if (a.pt_ok) {
     if (threadIdx.x == 0) {
-      const bool hc = ((blks[0] << a.b) & a.cmask_high) == a.cmask_high;
+      const bool hc = ((blk_of(0) << a.b) & a.cmask_high) == a.cmask_high;
       const bool unit_rule = kFast && (a.pt_ok & 2) && fF >= 0;
       unsigned int dmask = 0;
       int npt = 0;
@@ -292,14 +297,14 @@ __device__ __forceinline__ void pass_group(Worker<Real>& w, const PassArgs& a, c
         if (unit_rule) {
           const int c = hc ? a.pt_src[g] : g;
           if (c >= 0) {
-            const unsigned int mm = a.in_info[blks[c]].maxq_mode;
+            const unsigned int mm = a.in_info[blk_of(c)].maxq_mode;
             if (!(mm & 0x80000000u) && (long long)(mm & 0x1FFFFFFFu) <= (long long)fqsafe) src = c;
           }
         }
         if (src < 0) {
           bool zero = true;
           for (int h = 0; h < a.G; ++h)
-            if (((reads >> h) & 1u) && (a.in_info[blks[h]].maxq_mode & 0x9FFFFFFFu)) zero = false;
+            if (((reads >> h) & 1u) && (a.in_info[blk_of(h)].maxq_mode & 0x9FFFFFFFu)) zero = false;
           if (zero) src = g;
         }
         w.m->pt[g] = src;
@@ -312,7 +317,7 @@ __device__ __forceinline__ void pass_group(Worker<Real>& w, const PassArgs& a, c
     __syncthreads();
     any_pt = w.m->npt > 0;
     if (w.m->npt == a.G) {
-      for (int g = 0; g < a.G; ++g) w.pass_through(blks[w.m->pt[g]], blks[g], a);
+      for (int g = 0; g < a.G; ++g) w.pass_through(blk_of(w.m->pt[g]), blk_of(g), a);
       return;
     }
   }
@@ -332,25 +337,25 @@ __device__ __forceinline__ void pass_group(Worker<Real>& w, const PassArgs& a, c
     // ---- Decompress(S) ----
     for (int g = 0; g < a.G; ++g) {
       if (a.input_basis) {
-        const int pos = ((a.basis >> a.b) == blks[g]) ? 2 * (int)(a.basis & (unsigned long long)(B - 1)) : -1;
+        const int pos = ((a.basis >> a.b) == blk_of(g)) ? 2 * (int)(a.basis & (unsigned long long)(B - 1)) : -1;
         w.load_basis(g, pos);
       } else if (any_pt && !((w.m->dmask >> g) & 1u)) {
         w.load_basis(g, -1);  // read by no recoded block: zeros
       } else {
-        w.decode(g, a.in_arena + a.in_off[blks[g]], a.in_len[blks[g]]);
+        w.decode(g, a.in_arena + a.in_off[blk_of(g)], a.in_len[blk_of(g)]);
       }
     }
     // ---- Normalize(S) and GateComputation(G, S), tuple by tuple, in place ----
     if constexpr (KM > 8) {
       __syncthreads();  // every block of the group is decoded
-      big_gate_stage<Real>(w, a, (const BigGate*)fgv, sigma, blks[0]);
+      big_gate_stage<Real>(w, a, (const BigGate*)fgv, sigma, blk_of(0));
     }
     if constexpr (KM <= 8) {
     const int ntup = B >> a.nlow;
     for (int u = threadIdx.x; u < ntup; u += blockDim.x) {
       unsigned long long o = (unsigned long long)u;
       for (int l = 0; l < a.nlow; ++l) o = insert_zero_bit(o, a.low_t[l]);
-      const unsigned long long gidx = (blks[0] << a.b) | o;
+      const unsigned long long gidx = (blk_of(0) << a.b) | o;
       const bool ctrl = a.apply_gate && ((gidx & a.cmask) == a.cmask);
       const int bp = 2 * (int)o;
       if (kFast && fg->F >= 0) {
@@ -431,7 +436,7 @@ __device__ __forceinline__ void pass_group(Worker<Real>& w, const PassArgs& a, c
           if (exact_mask) {
   #pragma unroll
             for (int e = 0; e < 2 * KM; ++e)
-              if ((exact_mask >> e) & 1u) zx[e] = exact_component(a, sigma, qv, e >> 1, e & 1, ctrl);
+              if ((exact_mask >> e) & 1u) zx[e] = exact_component<KM>(a, sigma, qv, e >> 1, e & 1, ctrl);
           }
   #pragma unroll
           for (int mm = 0; mm < KM; ++mm)
@@ -453,15 +458,15 @@ __device__ __forceinline__ void pass_group(Worker<Real>& w, const PassArgs& a, c
     if (round == 0) {
       // ---- Compress(S) ----
       for (int g = 0; g < a.G; ++g) {
-        if (any_pt && w.m->pt[g] >= 0) w.pass_through(blks[w.m->pt[g]], blks[g], a);
-        else w.encode(g, blks[g], a);
+        if (any_pt && w.m->pt[g] >= 0) w.pass_through(blk_of(w.m->pt[g]), blk_of(g), a);
+        else w.encode(g, blk_of(g), a);
       }
     } else {
       // the raw values are in place: the verbatim sums of those blocks
       for (int g = 0; g < a.G; ++g)
         if (w.m->vbig[g]) {
           const double vs = w.verbatim_square_tree(g);
-          if (threadIdx.x == 0 && a.vsum) a.vsum[blks[g]] = vs;
+          if (threadIdx.x == 0 && a.vsum) a.vsum[blk_of(g)] = vs;
         }
       __syncthreads();
       if (threadIdx.x == 0) w.m->fix = 0;
