@@ -848,72 +848,78 @@ struct Worker {
 // equal weight. Writes wint[k] (internal node k = node D + k) and parent[v] for every node but
 // the root (2D - 2).
 //
-// All threads, in rounds rather than D - 1 serial steps. The steps consume the nodes in the
-// order of S, the merge of the leaf list with the internal-node list (leaves first on equal
-// weight), and internal node k joins S[2k] and S[2k + 1]. With m entries of S placed, the
-// internal nodes 0 .. m/2 - 1 are known, and every node not yet formed weighs at least
-// thr = S[m-1] + v0 (m odd) or 2 v0 (m even), v0 the lightest node available now. Every
-// available node of weight <= thr therefore precedes every unformed one (a leaf wins a tie;
-// a known internal node was formed earlier), so one round places all of them at once, each at
-// its merge position, and forms the internal nodes their pairs complete. thr at least doubles
-// every round, so a block (total weight < 2^16) needs at most 17 rounds. sw, sid: scratch for
-// S (weights and node ids, 2D - 2 entries each).
+// In rounds rather than D - 1 serial steps. The steps consume the nodes in the order of S, the
+// merge of the leaf list with the internal-node list (leaves first on equal weight), and
+// internal node k joins S[2k] and S[2k + 1]. With m entries of S placed, the internal nodes
+// 0 .. m/2 - 1 are known, and every node not yet formed weighs at least thr = S[m-1] + v0
+// (m odd) or 2 v0 (m even), v0 the lightest node available now. Every available node of
+// weight <= thr therefore precedes every unformed one (a leaf wins a tie; a known internal
+// node was formed earlier), so one round places all of them at once, each at its merge
+// position, and forms the internal nodes their pairs complete. thr at least doubles every
+// round, so a block (total weight < 2^16) needs at most 17 rounds. One warp runs the rounds
+// (warp votes and warp barriers only); the CTA waits once, after it. sw, sid: scratch for S
+// (weights and node ids, 2D - 2 entries each).
 __device__ inline void huffman_merge(const uint32_t* keys, int D, uint32_t* wint, uint16_t* parent,
                                      uint32_t* sw, uint16_t* sid) {
-  const int tid = threadIdx.x, T = blockDim.x;
-  int m = 0, lp = 0, ip = 0;  // S entries placed, leaves and internal nodes consumed (uniform)
-  while (m < 2 * D - 2) {
-    const int nk = m >> 1;  // internal nodes formed
-    uint32_t v0 = 0xFFFFFFFFu;
-    if (lp < D) v0 = keys[lp] >> 16;
-    if (ip < nk && wint[ip] < v0) v0 = wint[ip];
-    const uint32_t thr = (m & 1) ? sw[m - 1] + v0 : 2u * v0;
-    // available nodes at or below thr (each list is sorted, so they are prefixes)
-    int cl = 0, ci = 0;
-    for (int t0 = 0; t0 < D - lp; t0 += T) {
-      const int t = t0 + tid;
-      cl += __syncthreads_count(t < D - lp && (keys[lp + t] >> 16) <= thr);
-    }
-    for (int t0 = 0; t0 < nk - ip; t0 += T) {
-      const int t = t0 + tid;
-      ci += __syncthreads_count(t < nk - ip && wint[ip + t] <= thr);
-    }
-    // merge positions: a leaf follows the internal nodes lighter than it, an internal node
-    // follows the leaves not heavier than it
-    for (int t = tid; t < cl; t += T) {
-      const uint32_t x = keys[lp + t] >> 16;
-      int lo = ip, hi = ip + ci;
-      while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (wint[mid] < x) lo = mid + 1;
-        else hi = mid;
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    int m = 0, lp = 0, ip = 0;  // S entries placed, leaves and internal nodes consumed (uniform)
+    while (m < 2 * D - 2) {
+      const int nk = m >> 1;  // internal nodes formed
+      uint32_t v0 = 0xFFFFFFFFu;
+      if (lp < D) v0 = keys[lp] >> 16;
+      if (ip < nk && wint[ip] < v0) v0 = wint[ip];
+      const uint32_t thr = (m & 1) ? sw[m - 1] + v0 : 2u * v0;
+      // available nodes at or below thr (each list is sorted, so they form prefixes)
+      int cl = 0, ci = 0;
+      for (int t0 = 0; t0 < D - lp; t0 += 32) {
+        const unsigned v = __ballot_sync(0xffffffffu, t0 + lane < D - lp && (keys[lp + t0 + lane] >> 16) <= thr);
+        cl += __popc(v);
+        if (v != 0xffffffffu) break;
       }
-      sw[m + t + (lo - ip)] = x;
-      sid[m + t + (lo - ip)] = (uint16_t)(lp + t);
-    }
-    for (int t = tid; t < ci; t += T) {
-      const uint32_t x = wint[ip + t];
-      int lo = lp, hi = lp + cl;
-      while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if ((keys[mid] >> 16) <= x) lo = mid + 1;
-        else hi = mid;
+      for (int t0 = 0; t0 < nk - ip; t0 += 32) {
+        const unsigned v = __ballot_sync(0xffffffffu, t0 + lane < nk - ip && wint[ip + t0 + lane] <= thr);
+        ci += __popc(v);
+        if (v != 0xffffffffu) break;
       }
-      sw[m + t + (lo - lp)] = x;
-      sid[m + t + (lo - lp)] = (uint16_t)(D + ip + t);
+      // merge positions: a leaf follows the internal nodes lighter than it, an internal node
+      // follows the leaves not heavier than it
+      for (int t = lane; t < cl; t += 32) {
+        const uint32_t x = keys[lp + t] >> 16;
+        int lo = ip, hi = ip + ci;
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if (wint[mid] < x) lo = mid + 1;
+          else hi = mid;
+        }
+        sw[m + t + (lo - ip)] = x;
+        sid[m + t + (lo - ip)] = (uint16_t)(lp + t);
+      }
+      for (int t = lane; t < ci; t += 32) {
+        const uint32_t x = wint[ip + t];
+        int lo = lp, hi = lp + cl;
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if ((keys[mid] >> 16) <= x) lo = mid + 1;
+          else hi = mid;
+        }
+        sw[m + t + (lo - lp)] = x;
+        sid[m + t + (lo - lp)] = (uint16_t)(D + ip + t);
+      }
+      __syncwarp();
+      const int mn = m + cl + ci;
+      for (int k = nk + lane; k < (mn >> 1); k += 32) {
+        wint[k] = sw[2 * k] + sw[2 * k + 1];
+        parent[sid[2 * k]] = (uint16_t)(D + k);
+        parent[sid[2 * k + 1]] = (uint16_t)(D + k);
+      }
+      __syncwarp();
+      m = mn;
+      lp += cl;
+      ip += ci;
     }
-    __syncthreads();
-    const int mn = m + cl + ci;
-    for (int k = nk + tid; k < (mn >> 1); k += T) {
-      wint[k] = sw[2 * k] + sw[2 * k + 1];
-      parent[sid[2 * k]] = (uint16_t)(D + k);
-      parent[sid[2 * k + 1]] = (uint16_t)(D + k);
-    }
-    __syncthreads();
-    m = mn;
-    lp += cl;
-    ip += ci;
   }
+  __syncthreads();
 }
 
 // Depth of every node of the merged tree by pointer jumping (all threads): d[v] += d[p[v]],
