@@ -619,6 +619,11 @@ def run_full_circuit(args):
     if args.dtype:
         wl["dtype"] = {"c128": 2, "c64": 1}[args.dtype]
     n, gates = wl["n"], wl["gates"]
+    unfused = len(gates)
+    if args.fuse:
+        # gates fused into dense unitaries of up to 5 qubits (at most 2 at or above the block);
+        # amplitude-updates still count the original circuit's gates
+        gates = C.fuse(gates, 5, block_log2=wl["block_log2"])
     pool = sv.Pool(int((args.pool_gb or wl.get("pool_gb", 8.0)) * (1 << 30)))
     st = sv.State(pool, n, wl["slice_log2"], wl["eb"], wl["dtype"], block_log2=wl["block_log2"],
                   arena_bytes=args.arena_mb << 20)
@@ -663,10 +668,12 @@ def run_full_circuit(args):
         "workload": wl["desc"], "dtype": wl["dtype"], "eb": wl["eb"],
         "block_log2": wl["block_log2"], "threads_per_cta": args.threads or "default",
         "register_capped_build": args.compact, "huffman_chunk": args.chunk or 32,
-        "gates": len(gates), "blocks_reused_fraction": reused / (len(gates) * stt["n_blocks"]),
+        "gates": unfused, "passes": len(gates), "fused": bool(args.fuse),
+        "blocks_reused_fraction": reused / (len(gates) * stt["n_blocks"]),
         "replayed_passes": stt["replayed_passes"],
-        "amp_updates_per_s_wall": (1 << n) * len(gates) / wall,
-        "amp_updates_per_s_kernel": (1 << n) * npass / (kern_ms * 1e-3) if kern_ms else None,
+        "amp_updates_per_s_wall": (1 << n) * unfused / wall,
+        "amp_updates_per_s_kernel": (1 << n) * unfused / (kern_ms * 1e-3) if kern_ms else None,
+        "passes_per_s_kernel": npass / (kern_ms * 1e-3) if kern_ms else None,
         "kernel_ms_total": kern_ms, "wall_s": wall, "fused_kernel_gbs": alg_bytes / (kern_ms * 1e-3) / 1e9,
         "fidelity_vs_closed_form": fid,
         "compression_ratio_final": raw / per_gate[-1], "compression_ratio_min": raw / max(per_gate),
@@ -680,20 +687,35 @@ def run_full_circuit(args):
     }
     if fid is None and args.plain:
         # no closed form: the plain GPU path runs the whole circuit beside the compressed
-        # state and the fidelity is taken between the two final states
+        # state. The fidelity reference is the FP64 (complex128) plain state whatever the
+        # compressed dtype, so a complex64 run states its error against FP64; the plain path of
+        # the compressed run's own dtype is what the speed is compared with.
         try:
-            ppool = sv.Pool(raw + (256 << 20))
-            ps = sv.State(ppool, n, n, 0.0, wl["dtype"])
-            ps.reset_basis(x)
-            ps.sync()
+            raw128 = report.raw_state_bytes(n, 2)
+            ppool = sv.Pool(raw128 + (wl["dtype"] == 1) * raw + (256 << 20))
+            ref = sv.State(ppool, n, n, 0.0, 2)
+            ref.reset_basis(x)
+            ref.sync()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            ps.run(gates)
+            ref.run(gates)
             e1.record(stream)
             torch.cuda.synchronize()
-            res["plain_amp_updates_per_s_whole_circuit"] = (1 << n) * len(gates) / (e0.elapsed_time(e1) * 1e-3)
-            res["fidelity_vs_plain"] = st.fidelity(ps)
-            ps.close()
+            res["fidelity_vs_fp64_plain"] = st.fidelity(ref)
+            t_plain = e0.elapsed_time(e1)
+            if wl["dtype"] == 1:
+                ps = sv.State(ppool, n, n, 0.0, 1)
+                ps.reset_basis(x)
+                ps.sync()
+                e0.record(stream)
+                ps.run(gates)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                t_plain = e0.elapsed_time(e1)
+                res["fidelity_complex64_plain_vs_fp64_plain"] = ps.fidelity(ref)
+                ps.close()
+            res["plain_amp_updates_per_s_whole_circuit"] = (1 << n) * unfused / (t_plain * 1e-3)
+            ref.close()
             ppool.close()
         except Exception as ex:  # noqa: BLE001
             res["plain_amp_updates_per_s_whole_circuit"] = "unavailable: %s" % ex
@@ -793,6 +815,8 @@ def main():
     ap.add_argument("--no-fidelity", dest="fidelity", action="store_false")
     ap.add_argument("--full-circuit", action="store_true",
                     help="run the whole circuit once (per-gate sizes, closed-form fidelity)")
+    ap.add_argument("--fuse", action="store_true",
+                    help="full-circuit mode: fuse the circuit into dense gates of up to 5 qubits")
     ap.add_argument("--serve", action="store_true", help="serve the mixed request stream")
     ap.add_argument("--serve-count", type=int, default=2000)
     ap.add_argument("--serve-rate", type=float, default=20.0)

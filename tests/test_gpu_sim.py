@@ -395,3 +395,59 @@ def test_qft30_full_size_properties(sv):
     finally:
         st.close()
         pool.close()
+
+
+def test_qft22_at_the_qft34_block_shape_bit_exact(sv, pool):
+    """The whole QFT22 circuit with the launch shape of the QFT34 workload (2048-amplitude blocks,
+    2^20-amplitude slices, complex128, eb 1e-7, 256 threads, register-capped build): targets and
+    SWAP partners above the block, controls above the block and the slice, at full block size.
+    Streams are compared every 24 passes and at the end, the stored norm after every pass."""
+    n, sl, b, eb = 22, 20, 11, 1e-7
+    x = C.seeded_index(0, n)
+    gates = C.qft(n)
+    st = sv.State(pool, n, sl, eb, oracle.C128, block_log2=b)
+    try:
+        st.set_threads(256)
+        st.set_compact(True)
+        st.reset_basis(x)
+        cs = oracle.CompressedSim(n, sl, b, oracle.C128, eb, x)
+        for i, g in enumerate(gates):
+            st.apply(g.matrix, g.targets, g.controls)
+            cs.apply(g.matrix, g.targets, g.controls)
+            assert st.norm() == cs.norm, "gate %d" % i
+            if i % 24 == 23 or i == len(gates) - 1:
+                assert_same_state(st, cs, "gate %d %s %s %s" % (i, g.name, g.targets, g.controls))
+        F = st.fidelity_qft(x)
+        print("QFT22 at the QFT34 block shape: 1 - F = %.3e" % (1 - F))
+    finally:
+        st.close()
+
+
+@pytest.mark.parametrize("kind", ["qft", "random"])
+def test_complex64_fidelity_against_the_fp64_plain_oracle(sv, pool, kind):
+    """The FP32 variant's error against FP64: the complex64 compressed state (byte-exact with
+    the oracle's complex64 Algorithm 1) compared with the FP64 plain oracle (O1 in complex128)."""
+    n, sl, b, eb = 12, 10, 8, 1e-6
+    x = C.seeded_index(3, n) if kind == "qft" else 0
+    gates = C.qft(n) if kind == "qft" else C.random_brickwork(n, 6, seed=2)
+    st = sv.State(pool, n, sl, eb, oracle.C64, block_log2=b)
+    try:
+        st.reset_basis(x)
+        st.run(gates)
+        cs = oracle.CompressedSim(n, sl, b, oracle.C64, eb, x).run(gates)
+        assert_same_state(st, cs, "end")
+        ref = oracle.PlainSim(n, oracle.C128, x).run(gates).state
+        got = st.read()
+        F = abs(np.vdot(ref, got)) ** 2 / (np.vdot(got, got).real * np.vdot(ref, ref).real)
+        # the complex128 run at the same bound, for scale
+        st2 = sv.State(pool, n, sl, eb, oracle.C128, block_log2=b)
+        st2.reset_basis(x)
+        st2.run(gates)
+        got2 = st2.read()
+        st2.close()
+        F2 = abs(np.vdot(ref, got2)) ** 2 / (np.vdot(got2, got2).real * np.vdot(ref, ref).real)
+        print("%s%d eb %g: 1 - F complex64 vs FP64 = %.3e, complex128 vs FP64 = %.3e" % (kind, n, eb, 1 - F, 1 - F2))
+        # FP32 rounding (2^-24 relative) stays below the bound's quantization error here
+        assert 1 - F < 1e-6 and 1 - F < 10 * (1 - F2) + 1e-9
+    finally:
+        st.close()
