@@ -209,6 +209,13 @@ int sv_set_threads(sv_state* s, int threads);
  * depend on it. SV_ERR_ARG for a plain state. Batches ignore it. */
 int sv_set_compact(sv_state* s, int on);
 
+/* Apply 4- and 5-qubit complex128 gates on the tensor cores (on != 0, the default) or on the
+ * CUDA cores. An implementation choice with no counterpart in the paper: the tensor cores
+ * compute the fixed-point gate sums exactly through FP16 digit products (with the same
+ * tie-margin fallback to the FP64 chain), so streams and norms do not depend on it; passes on
+ * the tensor cores use 256-thread CTAs. SV_ERR_ARG for a plain state. */
+int sv_set_tensor_cores(sv_state* s, int on);
+
 /* Huffman chunk size of the state's block format: the number of symbols per stored chunk bit
  * count, each chunk decoded by one thread (16, 32 or 64; the default 32). Smaller chunks
  * decode with more threads in parallel and cost 16 more bits per chunk of stream. It changes

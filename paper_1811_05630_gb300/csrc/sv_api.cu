@@ -19,6 +19,7 @@
 
 #include "../../include/sv.h"
 #include "sv_internal.h"
+#include "sv_tc.cuh"
 
 using namespace sv;
 
@@ -138,6 +139,7 @@ struct sv_state {
   int threads = 0;                  // CTA size of the fused pass (0: default)
   bool compact = false;             // register-capped build of the pass (1- and 2-qubit gates)
   int huff_chunk = 32;              // Huffman chunk size of the block format
+  bool tensor_cores = true;         // 4- and 5-qubit complex128 gates on the tensor cores
   DevScalars* hsc = nullptr;        // pinned host copy of the device scalars
   bool hsc_valid = false;           // hsc holds the state after every submitted pass
   // passes between status checks (an overflow poisons every later pass until the check
@@ -276,6 +278,17 @@ void build_args(const sv_state* s, const Logged& lg, PassArgs& a) {
     }
     a.gbig = s->gslot;
     a.gfbig = s->gslotf;
+    // tensor cores for 4- and 5-qubit complex128 gates: 256-thread CTAs (the CTA size does not
+    // change results), the stage holds the 128-tuple operand tile, and the CTA's shared memory
+    // admits at most two CTAs per SM, whose tensor-memory columns then always fit
+    if (s->tensor_cores && s->dtype == SV_C128 && a.K > 8 && threads_ok(s->b, 256) &&
+        chunk_ok(s->b, s->huff_chunk, 256)) {
+      const Layout Lb = make_layout(s->b, a.G, 8, false, true);
+      if (Lb.stage_bytes >= (uint32_t)(kTcM * 2 * a.K * 2) && Lb.total + 1024 > 228u * 1024u / 3u) {
+        a.tc = 1;
+        a.threads = 256;
+      }
+    }
     // stream pass-through map: slot g keeps the codes of slot src when every row of the
     // members in g is a unit row (exactly 1) whose column is the same in-block position in
     // slot src; with in-block controls only src = g (the identity) qualifies
@@ -786,6 +799,12 @@ int sv_set_chunk(sv_state* s, int chunk) {
   if (rc) return rc;
   s->huff_chunk = chunk;
   return sv_reset_basis(s, 0);  // the stored streams were coded with the old chunk size
+}
+
+int sv_set_tensor_cores(sv_state* s, int on) {
+  if (!s || s->plain) return SV_ERR_ARG;
+  s->tensor_cores = on != 0;
+  return SV_OK;
 }
 
 int sv_set_compact(sv_state* s, int on) {

@@ -41,6 +41,7 @@ struct Misc {
   int pt[4];       // pass-through source slot per block of the group (-1: recode)
   unsigned int dmask;  // blocks of the group to decode
   int npt;
+  int tc_nx, tc_over;  // tensor-core gate: outputs listed for the exact chain, list overflow
   int first[34];   // canonical first code per length
   int offs[34];    // first canonical index per length
   int lcount[34];  // codes per length
@@ -76,6 +77,7 @@ struct __align__(16) PassArgs {
   double two2;
   double two_r;       // fl(2eb * r), the dequantize-requantize factor (about 1)
   unsigned long long ngroups;
+  int tc;  // 4- and 5-qubit gates of complex128 on the tensor cores (256-thread CTAs)
   const uint8_t* in_arena;
   const unsigned long long* in_off;
   const unsigned int* in_len;
@@ -121,18 +123,25 @@ struct FastGate {
 };
 
 // Fixed-point form of a 4- or 5-qubit gate (K = 16 or 32 members per tuple) for complex128,
-// prepared by all threads of a CTA: the same quantities as FastGate, with the coefficient
-// tables transposed (entry ((m * 2 + c) * 2 + p) * K + jj) so that the lanes of a warp, which
-// take consecutive output rows jj of one tuple, read consecutive words. complex64 keeps the
-// FP32 matrix in the chi area instead (entry 2 (m K + jj) + {0: re, 1: im}).
-struct BigGate {
+// prepared by all threads of a CTA: the same quantities as FastGate. The table area holds one
+// of two forms of the coefficients v = round(c 2^(F+31)) (c = sigma G fl(2eb r)):
+//  - CUDA-core form: v split as hi 2^31 + lo, transposed (entry ((m * 2 + c) * 2 + p) * K + jj,
+//    hi in tab[0, 4096), lo in tab[4096, 8192)) so that the lanes of a warp, which take
+//    consecutive output rows jj of one tuple, read consecutive words;
+//  - tensor-core form: v as 7 balanced base-512 digits (v = sum_d dig_d 512^d, |dig_d| <= 256),
+//    each digit an FP16 matrix of 2K output rows by 2K input columns in the tensor cores'
+//    no-swizzle K-major layout (see sv_pass_tc.cuh), digit d at byte 2 d (2K)^2.
+// complex64 keeps the FP32 matrix in the table area instead (entry 2 (m K + jj) + {0: re, 1: im}).
+struct __align__(128) BigGate {
+  int32_t tab[7 * 64 * 64 / 2];  // 56 KB: 7 FP16 matrices of 64 x 64 (the larger form)
   int F, diag, real, qsafe;
   long long margin;
   int32_t idhi, idlo;
   double rows[32];  // row sums of |c| (scratch of the preparation)
   int8_t ssrc[32][2], ssgn[32][2];
-  int32_t chi[4 * 32 * 32];
-  int32_t clo[4 * 32 * 32];
+  unsigned long long mbar;  // tensor-core form: completion barrier of the CTA's MMAs
+  uint32_t tmem;            // tensor-core form: the CTA's tensor-memory columns
+  int tc;                   // the table holds the tensor-core form
 };
 
 // Dynamic shared-memory layout of a worker CTA (host and device agree on it).
@@ -178,6 +187,7 @@ __host__ __device__ inline Layout make_layout(int b, int G, int csize, bool batc
   o += (uint32_t)(L.hs * 4);
   // stream image: header + largest body (PACK at 32 bits) + verbatim section
   L.stage_bytes = (uint32_t)pad_to(kHdr + (size_t)L.nv * 4 + 2 * kVmax + 8 + (size_t)kVmax * csize + 16, 16);
+  if (big) o = (uint32_t)pad_to(o, 128);  // the stage doubles as a tensor-core operand tile
   L.off_stage = o;
   o += L.stage_bytes;
   // codebook build: keys, vals (p2cap each), internal weights (dcap), parent and its
@@ -198,6 +208,7 @@ __host__ __device__ inline Layout make_layout(int b, int G, int csize, bool batc
   o += L.build_bytes;
   L.off_misc = o;
   o += (uint32_t)pad_to(sizeof(Misc), 16);  // scalars and scan workspace
+  if (big) o = (uint32_t)pad_to(o, 128);    // tensor-core operand tables
   L.off_fast = o;
   o += (uint32_t)pad_to(big ? sizeof(BigGate) : sizeof(FastGate), 16);
   L.off_desc = o;  // the batched pass keeps the current state's descriptor here

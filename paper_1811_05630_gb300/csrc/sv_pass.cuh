@@ -3,6 +3,7 @@
 // translation units that instantiate k_pass (with and without a register cap).
 #pragma once
 #include "sv_internal.h"
+#include "sv_tc.cuh"
 
 namespace sv {
 
@@ -240,7 +241,7 @@ __device__ __forceinline__ void tuple_exact(Worker<Real>& w, const PassArgs& a, 
 // fgv: the CTA's FastGate (KM <= 8) or BigGate (KM = 32), prepared before the first group
 template <typename Real, int KM>
 __device__ __forceinline__ void pass_group(Worker<Real>& w, const PassArgs& a, const void* __restrict__ fgv,
-                                           double sigma, unsigned long long grp) {
+                                           double sigma, unsigned long long grp, uint32_t* tc_par = nullptr) {
   using A = Arith<Real>;
   const Layout& L = w.L;
   const FastGate* __restrict__ fg = (const FastGate*)fgv;
@@ -348,7 +349,7 @@ __device__ __forceinline__ void pass_group(Worker<Real>& w, const PassArgs& a, c
     // ---- Normalize(S) and GateComputation(G, S), tuple by tuple, in place ----
     if constexpr (KM > 8) {
       __syncthreads();  // every block of the group is decoded
-      big_gate_stage<Real>(w, a, (const BigGate*)fgv, sigma, blk_of(0));
+      big_gate_stage<Real>(w, a, (BigGate*)fgv, sigma, blk_of(0), tc_par);
     }
     if constexpr (KM <= 8) {
     const int ntup = B >> a.nlow;
@@ -483,6 +484,17 @@ __device__ __forceinline__ void pass_body(const PassArgs& a) {
   if (a.chunk) w.kc = a.chunk;
   // A state poisoned by an earlier pass (or by another CTA of this one) is skipped. One
   // thread reads the flag so that the whole CTA takes the same branch.
+  uint32_t tc_par = 0;  // phase of the CTA's tensor-core completion barrier
+  if constexpr (KM > 8) {
+    if (a.tc) {  // tensor-memory columns and the completion barrier for the whole kernel
+      BigGate* bgp = (BigGate*)(smem + L.off_fast);
+      if (threadIdx.x < 32) tc_alloc(&bgp->tmem);
+      if (threadIdx.x == 0) tc_mbar_init(&bgp->mbar);
+      tc_fence_before_sync();
+      __syncthreads();
+      tc_fence_after_sync();
+    }
+  }
   if (threadIdx.x == 0) {
     w.m->err = 0;
     w.m->live = *(volatile unsigned int*)&a.sc->status == 0;
@@ -497,18 +509,27 @@ __device__ __forceinline__ void pass_body(const PassArgs& a) {
       if (sizeof(Real) == 8 && threadIdx.x == 0) fast_prepare((FastGate*)fg, a, sigma);  // visible after pass_group's barrier
     }
     for (unsigned long long grp = blockIdx.x; grp < a.ngroups; grp += gridDim.x)
-      pass_group<Real, KM>(w, a, fg, sigma, grp);
+      pass_group<Real, KM>(w, a, fg, sigma, grp, &tc_par);
     if (threadIdx.x == 0 && w.m->err) {
       atomicOr(&a.sc->status, w.m->err);
       atomicMin(&a.sc->fail_seq, a.seq);
+    }
+  }
+  if constexpr (KM > 8) {
+    if (a.tc) {  // every MMA has completed (each was waited for) and every load is done
+      tc_fence_before_sync();
+      __syncthreads();
+      if (threadIdx.x < 32) tc_dealloc(((BigGate*)(smem + L.off_fast))->tmem);
     }
   }
 }
 
 // The pass kernel without a register cap, and (COMPACT) with one: 64 registers per thread,
 // spilling, so that four 256-thread CTAs fit on an SM.
+// 4- and 5-qubit gates (KM = 32): at most 128 registers, so that the two CTAs per SM that the
+// shared memory admits also fit the register file
 template <typename Real, int KM>
-__global__ void __launch_bounds__(256) k_pass(const PassArgs a) {
+__global__ void __launch_bounds__(256, KM > 8 ? 2 : 1) k_pass(const PassArgs a) {
   pass_body<Real, KM>(a);
 }
 template <typename Real, int KM>
@@ -530,6 +551,19 @@ static cudaError_t launch_pass_k(const PassArgs& a, cudaStream_t st) {
   const int T = threads_ok(a.b, a.threads) ? a.threads : worker_threads(a.b);
   if (!chunk_ok(a.b, a.chunk ? a.chunk : kChunkDefault, T)) return cudaErrorInvalidValue;
   unsigned long long grid = a.ngroups;
+  if constexpr (KM > 8) {
+    // 4- and 5-qubit gates: as many CTAs as fit at once, each walking many groups, so that the
+    // per-CTA preparation of the gate's coefficient tables (and tensor memory) is amortized
+    // (resident CTAs per SM: what the 228 KB of shared memory holds, each CTA with the 1 KB the
+    // hardware reserves, and at most two by the 128-register cap of this build)
+    int dev = 0, sms = 0;
+    int per_sm = (int)((228u * 1024u) / (L.total + 1024u));
+    if (per_sm > 2) per_sm = 2;
+    if (per_sm < 1) per_sm = 1;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+        sms > 0 && grid > (unsigned long long)sms * per_sm)
+      grid = (unsigned long long)sms * per_sm;
+  }
   if (grid > 0x7fffffffull) grid = 0x7fffffffull;
   if constexpr (COMPACT) k_pass_c<Real, KM><<<(unsigned int)grid, T, L.total, st>>>(a);
   else k_pass<Real, KM><<<(unsigned int)grid, T, L.total, st>>>(a);

@@ -22,13 +22,16 @@ template <typename Real>
 __device__ inline void big_prepare(BigGate* bg, const PassArgs& a, double sigma) {
   const int K = a.K, tid = threadIdx.x, T = blockDim.x;
   if (sizeof(Real) == 4) {
-    float* gfs = (float*)bg->chi;
+    float* gfs = (float*)bg->tab;
     for (int e = tid; e < K * K; e += T) {
       const int jj = e / K, m = e % K;  // row-major input: entry e = jj K + m
       gfs[2 * (m * K + jj)] = a.gfbig[2 * e];
       gfs[2 * (m * K + jj) + 1] = a.gfbig[2 * e + 1];
     }
-    if (tid == 0) bg->F = -1;
+    if (tid == 0) {
+      bg->F = -1;
+      bg->tc = 0;
+    }
     __syncthreads();
     return;
   }
@@ -76,6 +79,7 @@ __device__ inline void big_prepare(BigGate* bg, const PassArgs& a, double sigma)
     bg->F = F;
     bg->diag = 1;
     bg->real = 1;
+    bg->tc = 0;
     if (F >= 0) {
       // the exact chain lands within (K + 7) 2^-53 R Q of T (K - 1 ordered additions, the
       // decode, scale, product, difference and requantization roundings, and the roundings of
@@ -94,7 +98,40 @@ __device__ inline void big_prepare(BigGate* bg, const PassArgs& a, double sigma)
   }
   __syncthreads();
   const int F = bg->F;
+  if (F >= 0 && a.tc) {
+    // tensor-core form: the digits of v for output row o = 2 jj + p and input column
+    // i = 2 m + c, one FP16 matrix per digit in the no-swizzle K-major layout
+    if (tid == 0) {
+      bg->tc = 1;
+      bg->diag = 0;  // the diagonal and real shortcuts read the CUDA-core tables
+      bg->real = 0;
+    }
+    const double scale = scalbn(1.0, F + 31);
+    const int kin = 2 * K;
+    uint16_t* dig = (uint16_t*)bg->tab;
+    for (int e = tid; e < K * K; e += T) {
+      const int jj = e / K, m = e % K;
+      const double A = __dmul_rn(__ldg(a.gbig + 2 * e), s1);
+      const double Bc = __dmul_rn(__ldg(a.gbig + 2 * e + 1), s1);
+      const double cv[4] = {A, Bc, -Bc, A};  // (c, p) = (0, 0), (0, 1), (1, 0), (1, 1)
+      for (int cp = 0; cp < 4; ++cp) {
+        long long v = __double2ll_rn(__dmul_rn(cv[cp], scale));
+        const int o = 2 * jj + (cp & 1), i = 2 * m + (cp >> 1);
+        for (int d = 0; d < kTcDigits; ++d) {
+          const long long t = v + 256;
+          const long long hi = t >> 9;  // floor
+          const int digit = (int)(t - (hi << 9)) - 256;
+          v = hi;
+          dig[d * kin * kin + tc_tile_index(o, i, kin)] = __half_as_ushort(__int2half_rn(digit));
+        }
+      }
+    }
+    tc_fence_operands();
+    __syncthreads();
+    return;
+  }
   if (F >= 0) {
+    if (tid == 0) bg->tc = 0;
     const double scale = scalbn(1.0, F + 31);
     bool diag = true, real = true;
     for (int e = tid; e < K * K; e += T) {
@@ -108,8 +145,8 @@ __device__ inline void big_prepare(BigGate* bg, const PassArgs& a, double sigma)
       for (int cp = 0; cp < 4; ++cp) {
         const long long v = __double2ll_rn(__dmul_rn(cv[cp], scale));
         const int idx = (m * 4 + cp) * K + jj;
-        bg->chi[idx] = (int32_t)(v >> 31);
-        bg->clo[idx] = (int32_t)(v & 0x7fffffffll);
+        bg->tab[idx] = (int32_t)(v >> 31);
+        bg->tab[4096 + idx] = (int32_t)(v & 0x7fffffffll);
       }
     }
     if (!diag) atomicAnd(&bg->diag, 0);
@@ -132,7 +169,7 @@ __device__ __forceinline__ void big_exact_row(const Worker<Real>& w, const PassA
     *zi = a.use_sigma ? A::mul(sg, xi) : xi;
     return;
   }
-  const float* gfs = (const float*)bg->chi;
+  const float* gfs = (const float*)bg->tab;
   Real ar = 0, ai = 0;
   for (int m = 0; m < K; ++m) {
     const int p = bp + a.pos_delta[m];
@@ -163,19 +200,21 @@ __device__ __forceinline__ void big_exact_row(const Worker<Real>& w, const PassA
   *zi = ai;
 }
 
-// GateComputation for one group (codes decoded in w.q), in place. All threads call it; it
-// ends with a barrier.
+// GateComputation for the tuples [u0, u1) of one group (codes decoded in w.q), in place, on
+// the CUDA cores: rounds of blockDim.x output rows. `tables`: the CTA holds the CUDA-core form
+// of the fixed-point coefficients (otherwise every row runs the exact chain). All threads call
+// it; it ends with a barrier.
 template <typename Real>
-__device__ void big_gate_stage(Worker<Real>& w, const PassArgs& a, const BigGate* bg, double sigma,
-                               unsigned long long blk0) {
+__device__ void big_rounds(Worker<Real>& w, const PassArgs& a, const BigGate* bg, double sigma,
+                           unsigned long long blk0, int u0, int u1, bool tables) {
   const int K = a.K, T = blockDim.x, tid = threadIdx.x;
-  const int B = w.L.nv / 2, nv = w.L.nv;
+  const int nv = w.L.nv;
   const Real sg = (Real)sigma;
-  const int items = (B << a.h);  // one output row per amplitude of the group
-  const bool fast = sizeof(Real) == 8 && bg->F >= 0;
-  for (int r0 = 0; r0 < items; r0 += T) {
+  const bool fast = sizeof(Real) == 8 && bg->F >= 0 && tables;
+  for (int r0 = u0 * K; r0 < u1 * K; r0 += T) {
     const int it = r0 + tid;
-    const int u = it / K, jj = it % K;
+    const bool act = it < u1 * K;  // rows past the range recompute row u0 * K and write nothing
+    const int u = act ? it / K : u0, jj = act ? it % K : 0;
     unsigned long long o = (unsigned long long)u;
     for (int l = 0; l < a.nlow; ++l) o = insert_zero_bit(o, a.low_t[l]);
     const bool ctrl = ((((blk0 << a.b) | o) & a.cmask) == a.cmask);
@@ -214,16 +253,16 @@ __device__ void big_gate_stage(Worker<Real>& w, const PassArgs& a, const BigGate
           for (int c = 0; c < 2; ++c) {
             const long long qq = w.q[pm + c];
             const int idx = (jj * 4 + c * 2 + p) * K + jj;
-            sh += qq * bg->chi[idx];
-            sl += (qq * bg->clo[idx]) >> 4;
+            sh += qq * bg->tab[idx];
+            sl += (qq * bg->tab[4096 + idx]) >> 4;
           }
         } else {
           for (int m = 0; m < K; ++m) {
             const int pm = bp + a.pos_delta[m];
             const long long qr = w.q[pm], qi = w.q[pm + 1];
             const int i0 = (m * 4 + p) * K + jj, i1 = (m * 4 + 2 + p) * K + jj;
-            sh += qr * bg->chi[i0] + qi * bg->chi[i1];
-            sl += ((qr * bg->clo[i0]) >> 4) + ((qi * bg->clo[i1]) >> 4);
+            sh += qr * bg->tab[i0] + qi * bg->tab[i1];
+            sl += ((qr * bg->tab[4096 + i0]) >> 4) + ((qi * bg->tab[4096 + i1]) >> 4);
           }
         }
         if (!fast_round(sh + (sl >> 27), F, margin, &oc[p])) exact = true;
@@ -234,7 +273,8 @@ __device__ void big_gate_stage(Worker<Real>& w, const PassArgs& a, const BigGate
     __syncthreads();  // every row of this round has read its inputs
     const int pj = bp + a.pos_delta[jj];
     const int g = pj >> (w.b + 1), j = pj & (nv - 1);
-    if (exact) {
+    if (!act) {
+    } else if (exact) {
       w.put_value(g, j, zr);
       w.put_value(g, j + 1, zi);
     } else {
@@ -243,4 +283,21 @@ __device__ void big_gate_stage(Worker<Real>& w, const PassArgs& a, const BigGate
     }
   }
   __syncthreads();
+}
+
+#include "sv_pass_tc.cuh"
+
+// GateComputation for one group (codes decoded in w.q), in place: on the tensor cores when the
+// CTA holds the tensor-core form and the group's codes are small enough, else on the CUDA
+// cores. All threads call it; it ends with a barrier. tc_par: the CTA's mbarrier phase.
+template <typename Real>
+__device__ void big_gate_stage(Worker<Real>& w, const PassArgs& a, BigGate* bg, double sigma,
+                               unsigned long long blk0, uint32_t* tc_par) {
+  const int ntup = (w.L.nv / 2 << a.h) / a.K;
+  if (sizeof(Real) == 8 && bg->tc) {
+    if (tc_gate_stage<Real>(w, a, bg, sigma, blk0, tc_par)) return;
+    big_rounds<Real>(w, a, bg, sigma, blk0, 0, ntup, false);
+    return;
+  }
+  big_rounds<Real>(w, a, bg, sigma, blk0, 0, ntup, true);
 }

@@ -72,6 +72,7 @@ _SIGS = {
     "sv_sync": ([_vp], _i),
     "sv_set_threads": ([_vp, _i], _i),
     "sv_set_compact": ([_vp, _i], _i),
+    "sv_set_tensor_cores": ([_vp, _i], _i),
     "sv_set_chunk": ([_vp, _i], _i),
     "sv_measure_probs": ([_vp, _vp, _i, _vp], _i),
     "sv_amplitudes": ([_vp, _vp, _sz, _vp], _i),
@@ -182,6 +183,11 @@ class State:
     def set_chunk(self, chunk: int) -> None:
         """Huffman chunk size of the block format (16, 32, 64); resets the state to |0...0>."""
         _check(_L.sv_set_chunk(self._h, int(chunk)), "sv_set_chunk")
+
+    def set_tensor_cores(self, on: bool) -> None:
+        """4- and 5-qubit complex128 gates on the tensor cores (default) or the CUDA cores
+        (results unchanged)."""
+        _check(_L.sv_set_tensor_cores(self._h, 1 if on else 0), "sv_set_tensor_cores")
 
     def set_compact(self, on: bool) -> None:
         """Register-capped build of the fused pass for 1- and 2-qubit gates (results unchanged)."""

@@ -153,3 +153,56 @@ def test_batches_refuse_gates_above_3_qubits(sv, pool):
     finally:
         bt.close()
         st.close()
+
+
+def tc_gates(n, b, rng):
+    """Dense gates at 2048-amplitude blocks: inside the block, with two high targets (four blocks
+    per group: two chunks of 128 tuples), a 4-qubit gate under a control, a control above the
+    block, and unit / diagonal 5-qubit gates."""
+    perm = np.eye(32, dtype=np.complex128)[rng.permutation(32)]
+    perm[5] *= 1j
+    diag = np.diag(np.exp(2j * np.pi * rng.random(32)))
+    gates = [C.Gate(C.H, (q,), (), "H") for q in range(n)]
+    for t, c in [((0, 1, 2, 3, 4), ()), ((1, 3, b, 0, b + 1), ()), ((4, 2, 0, b + 2), (3,)),
+                 ((5, 6, 7, 8, 9), (b + 1,)), ((2, 9, 4, 10), ()), ((0, 1, 2, 3, 4), (5, 6))]:
+        gates.append(C.Gate(C.haar_unitary(len(t), rng), t, c, "U%d" % len(t)))
+    gates += [C.Gate(perm, (0, 2, 4, 6, 8), (), "P5"), C.Gate(diag, (1, 3, 5, 7, 9), (), "D5")]
+    return gates
+
+
+@pytest.mark.parametrize("eb", [1e-4, 1e-6, 1e-8])
+@pytest.mark.parametrize("tensor_cores", [True, False])
+def test_tensor_core_gate_bit_exact(sv, pool, eb, tensor_cores):
+    # eb 1e-4: every |code| < 256 (one code digit); 1e-6: two code digits; 1e-8: codes beyond
+    # the digit form (the CUDA-core rounds); each pass byte for byte against the oracle
+    n, sl, b = 14, 14, 11
+    gates = tc_gates(n, b, np.random.default_rng(int(-np.log10(eb))))
+    st = sv.State(pool, n, sl, eb, oracle.C128, block_log2=b)
+    try:
+        st.set_tensor_cores(tensor_cores)
+        st.reset_basis(0)
+        cs = oracle.CompressedSim(n, sl, b, oracle.C128, eb, 0)
+        for i, g in enumerate(gates):
+            st.apply(g.matrix, g.targets, g.controls)
+            cs.apply(g.matrix, g.targets, g.controls)
+            if g.k >= 4:
+                assert_same_state(st, cs, "gate %d %s %s %s" % (i, g.name, g.targets, g.controls))
+    finally:
+        st.close()
+
+
+def test_tensor_cores_do_not_change_fused_brickwork(sv, pool):
+    # a fused brickwork circuit at 2048-amplitude blocks, tensor cores on and off: equal streams
+    n, b, eb = 15, 11, 1e-6
+    fused = C.fuse(C.random_brickwork(n, 5, seed=9), 5, block_log2=b)
+    out = []
+    for tc in (True, False):
+        st = sv.State(pool, n, n, eb, oracle.C128, block_log2=b)
+        st.set_tensor_cores(tc)
+        st.reset_basis(0)
+        st.run(fused)
+        out.append(([st.block_stream(i) for i in range(1 << (n - b))], st.norm()))
+        st.close()
+    assert out[0] == out[1]
+    cs = oracle.CompressedSim(n, n, b, oracle.C128, eb, 0).run(fused)
+    assert out[0][0] == [cs.block_stream(i) for i in range(cs.nblocks)] and out[0][1] == cs.norm
