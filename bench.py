@@ -54,6 +54,14 @@ def workload(name: str):
                     basis=x, pool_gb=150.0, threads=256, compact=True,
                     desc="QFT on a random basis state, 34 qubits, complex128, eb 1e-7 abs, slice_log2 24, "
                          "compressed pool capped at 150 GB")
+    if name == "qft26p":
+        # the 34-qubit workload's codec work on a state ncu can capture: amplitudes 2^-13 at
+        # eb 1.6e-6 have the codes of amplitudes 2^-17 at eb 1e-7 (|q| about 38), same launch shape
+        n = 26
+        return dict(name="qft26p", n=n, eb=1.6e-6, slice_log2=24, block_log2=11, dtype=2, gates=C.qft(n),
+                    basis=C.seeded_index(0, n), pool_gb=8.0, threads=256, compact=True,
+                    desc="QFT on a random basis state, 26 qubits, complex128, eb 1.6e-6 abs (the codes of the "
+                         "34-qubit workload), slice_log2 24")
     if name == "qft12":
         n = 12
         return dict(name="qft12", n=n, eb=1e-6, slice_log2=8, block_log2=8, dtype=2, gates=C.qft(n),
@@ -375,7 +383,7 @@ def run_ours(args, rank, world, dist):
     tuned = None
     if args.block_log2:
         wl["block_log2"] = args.block_log2
-    elif args.autotune and n <= 30:
+    elif args.autotune and n <= 30 and not wl.get("threads"):
         from paper_1811_05630_gb300 import tune
 
         i0t = start_of_dense_stage(wl)
@@ -438,6 +446,8 @@ def run_ours(args, rank, world, dist):
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    if args.profile_window:  # ncu --profile-from-start off captures exactly the timed passes
+        torch.cuda.cudart().cudaProfilerStart()
     with ClockSampler(dev) as clk:
         for i, g in enumerate(timed):
             flush.fill_(i & 0xFF)
@@ -458,6 +468,8 @@ def run_ours(args, rank, world, dist):
             per_step_bytes.append(sti["compressed_bytes"])
         st.sync()
         torch.cuda.synchronize()
+    if args.profile_window:
+        torch.cuda.cudart().cudaProfilerStop()
     ms = sum(a.elapsed_time(c) for a, c in ev)
     kern_ms, npass, alg_bytes = st.pass_timing()
     stats = st.stats()
@@ -612,6 +624,16 @@ def run_full_circuit(args):
     from paper_1811_05630_gb300 import sv
 
     wl = workload(args.workload)
+    if args.n and args.n != wl["n"]:  # the same circuit family on another qubit count
+        n2 = args.n
+        if wl["name"].startswith("qft"):
+            wl.update(gates=C.qft(n2), basis=C.seeded_index(0, n2))
+        elif wl["name"].startswith("random"):
+            wl.update(gates=C.random_brickwork(n2, 20, seed=0))
+        else:
+            raise ValueError("--n applies to the QFT and random workloads")
+        wl["desc"] = wl["desc"].replace("%d qubits" % wl["n"], "%d qubits" % n2)
+        wl.update(n=n2, slice_log2=min(wl["slice_log2"], n2))
     if args.block_log2:
         wl["block_log2"] = args.block_log2
     if args.eb:
@@ -627,6 +649,10 @@ def run_full_circuit(args):
     pool = sv.Pool(int((args.pool_gb or wl.get("pool_gb", 8.0)) * (1 << 30)))
     st = sv.State(pool, n, wl["slice_log2"], wl["eb"], wl["dtype"], block_log2=wl["block_log2"],
                   arena_bytes=args.arena_mb << 20)
+    host = None
+    if args.spill_gb:  # arenas beyond the device pool go to pinned host memory
+        host = sv.Pool(int(args.spill_gb * (1 << 30)), "host")
+        st.set_spill(host)
     if args.threads:
         st.set_threads(args.threads)
     st.set_compact(args.compact)
@@ -683,6 +709,9 @@ def run_full_circuit(args):
         "marginal_probs_max_abs_dev_from_uniform": float(np.abs(p - 2.0 ** -m).max()),
         "sampled_prob_ratio_mean": float(samp.mean()), "sampled_prob_ratio_std": float(samp.std()),
         "pool_used_bytes": pool_used, "clocks": clk.summary(),
+        "spill_pool_gb": args.spill_gb or None,
+        "spill_used_bytes_end": host.usage()[0] if host is not None else None,
+        "spill_arena_bytes_end": stt.get("spill_arena_bytes"),
         "bytes_per_gate": per_gate,
     }
     if fid is None and args.plain:
@@ -799,7 +828,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="qft34", choices=["qft34", "grover20", "qft12", "random30"])
+    ap.add_argument("--workload", default="qft34", choices=["qft34", "qft26p", "grover20", "qft12", "random30"])
     ap.add_argument("--block-log2", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0, help="CTA size of the fused pass (0: tuned/default)")
     ap.add_argument("--compact", action="store_true", help="register-capped build of the fused pass")
@@ -815,6 +844,11 @@ def main():
     ap.add_argument("--no-fidelity", dest="fidelity", action="store_false")
     ap.add_argument("--full-circuit", action="store_true",
                     help="run the whole circuit once (per-gate sizes, closed-form fidelity)")
+    ap.add_argument("--n", type=int, default=0, help="full-circuit mode: the workload's circuit on n qubits")
+    ap.add_argument("--spill-gb", type=float, default=0.0,
+                    help="full-circuit mode: a pinned host-memory spill pool (GB) for arenas beyond the device pool")
+    ap.add_argument("--profile-window", action="store_true",
+                    help="bracket the timed passes with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     ap.add_argument("--fuse", action="store_true",
                     help="full-circuit mode: fuse the circuit into dense gates of up to 5 qubits")
     ap.add_argument("--serve", action="store_true", help="serve the mixed request stream")

@@ -77,6 +77,7 @@ typedef struct {
   uint64_t peak_compressed_bytes; /* largest compressed_bytes of any pass since the last
                                      sv_reset_basis: the paper's minimum compression ratio over
                                      a run (Sec. III) is the raw size divided by this */
+  uint64_t spill_arena_bytes;  /* capacity of the state's arenas held in its spill pool */
 } sv_stats_t;
 
 /* ---------------------------------------------------------------------------------------
@@ -85,7 +86,17 @@ typedef struct {
  * (2 MiB pages) to states. Returns SV_ERR_ARG on a NULL/misaligned pointer.
  * ------------------------------------------------------------------------------------- */
 int sv_pool_create(void* dev_base, size_t bytes, sv_pool** out);
-int sv_pool_destroy(sv_pool* pool); /* fails with SV_ERR_ARG while states remain */
+int sv_pool_destroy(sv_pool* pool); /* fails with SV_ERR_ARG while states or their pages remain */
+
+/* Spill pool (the paper's aim of fitting more qubits into a given memory, Sec. I and IV):
+ * sv_pool_create also accepts pinned host memory that the device can address (e.g. a pinned
+ * torch CPU tensor); the kernels then read and write its pages in host memory (over
+ * NVLink-C2C on a Grace system). sv_set_spill_pool(s, spill): arenas (the compressed streams)
+ * and measurement buffers of state s that do not fit in its pool are taken from `spill`
+ * (NULL: none); metadata and block tables stay in the state's pool. Results do not depend on
+ * where the arenas are. SV_ERR_ARG for a plain state or spill == the state's pool. The spill
+ * pool must outlive the state's use of it (sv_pool_destroy refuses while pages are held). */
+int sv_set_spill_pool(sv_state* s, sv_pool* spill);
 int sv_pool_usage(const sv_pool* pool, size_t* used_bytes, size_t* capacity_bytes);
 
 /* ---------------------------------------------------------------------------------------

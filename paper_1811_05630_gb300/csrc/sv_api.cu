@@ -32,8 +32,9 @@ size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 }  // namespace
 
 struct sv_pool {
-  uint8_t* base = nullptr;
+  uint8_t* base = nullptr;  // device-accessible address of the buffer
   size_t bytes = 0;
+  bool host = false;        // pinned host memory (a spill pool), reached over NVLink-C2C
   std::map<size_t, size_t> free_runs;  // offset -> length (bytes, page multiples)
   size_t used = 0;
   int nstates = 0;
@@ -89,6 +90,7 @@ struct Logged {
 struct Region {
   size_t off = 0, bytes = 0;
   bool live = false;
+  sv_pool* owner = nullptr;  // the pool the region lives in
 };
 
 }  // namespace
@@ -109,6 +111,7 @@ struct sv_state {
   Region gate_r;  // plain states (compressed states keep it in their metadata run)
   double* gslot = nullptr;
   float* gslotf = nullptr;
+  sv_pool* spill = nullptr;  // arenas and measurement buffers go here when `pool` is full
   // compressed
   unsigned long long nblocks = 0;
   Region meta_r, arena_r[2], aux_r;
@@ -164,12 +167,21 @@ bool region_alloc(sv_pool* p, Region* r, size_t bytes) {
   if (!p->alloc(bytes, &r->off)) return false;
   r->bytes = bytes;
   r->live = true;
+  r->owner = p;
   return true;
 }
 
 void region_free(sv_pool* p, Region* r) {
-  if (r->live) p->release(r->off, r->bytes);
+  (void)p;
+  if (r->live) r->owner->release(r->off, r->bytes);
   r->live = false;
+}
+
+uint8_t* region_ptr(const Region& r) { return r.owner->base + r.off; }
+
+// A region of the state's pool, else of its spill pool.
+bool region_alloc_spill(sv_state* s, Region* r, size_t bytes) {
+  return region_alloc(s->pool, r, bytes) || (s->spill && region_alloc(s->spill, r, bytes));
 }
 
 int status_to_err(unsigned int st) {
@@ -420,12 +432,12 @@ int reserve_arena(sv_state* s, int id, size_t want) {
   if (s->arena_r[id].bytes >= want) return SV_OK;
   const size_t old = s->arena_r[id].bytes;
   region_free(s->pool, &s->arena_r[id]);
-  if (!region_alloc(s->pool, &s->arena_r[id], want) && !region_alloc(s->pool, &s->arena_r[id], old)) {
+  if (!region_alloc_spill(s, &s->arena_r[id], want) && !region_alloc_spill(s, &s->arena_r[id], old)) {
     s->arena[id] = nullptr;  // no arena: the state takes no more passes
     s->sticky_err = SV_ERR_OOM;
     return SV_ERR_OOM;
   }
-  s->arena[id] = pool_ptr(s->pool, s->arena_r[id].off);
+  s->arena[id] = region_ptr(s->arena_r[id]);
   return SV_OK;
 }
 
@@ -434,12 +446,12 @@ int grow_arena(sv_state* s, int id, size_t need) {
   // further, and every overflow costs a replay
   size_t want = std::max(s->arena_r[id].bytes + s->arena_r[id].bytes / 2, 2 * need);
   region_free(s->pool, &s->arena_r[id]);
-  if (!region_alloc(s->pool, &s->arena_r[id], want) && !region_alloc(s->pool, &s->arena_r[id], need)) {
+  if (!region_alloc_spill(s, &s->arena_r[id], want) && !region_alloc_spill(s, &s->arena_r[id], need)) {
     s->arena[id] = nullptr;  // no arena: the state takes no more passes
     s->sticky_err = SV_ERR_OOM;
     return SV_ERR_OOM;
   }
-  s->arena[id] = pool_ptr(s->pool, s->arena_r[id].off);
+  s->arena[id] = region_ptr(s->arena_r[id]);
   return SV_OK;
 }
 
@@ -449,8 +461,8 @@ int ensure_aux(sv_state* s) {
   s->chunk_amps = std::min<unsigned long long>(dim, 1ull << 20);
   const size_t chunk_bytes = (size_t)s->chunk_amps * 16;
   const size_t bytes = 2 * chunk_bytes + (sizeof(double) << 16) + 64 + 4096;
-  if (!region_alloc(s->pool, &s->aux_r, bytes)) return SV_ERR_OOM;
-  uint8_t* p = pool_ptr(s->pool, s->aux_r.off);
+  if (!region_alloc_spill(s, &s->aux_r, bytes)) return SV_ERR_OOM;
+  uint8_t* p = region_ptr(s->aux_r);
   s->chunk[0] = (double*)p;
   s->chunk[1] = (double*)(p + chunk_bytes);
   s->bins = (double*)(p + 2 * chunk_bytes);
@@ -492,6 +504,17 @@ int sv_pool_create(void* dev_base, size_t bytes, sv_pool** out) {
   if (!dev_base || !out || ((uintptr_t)dev_base & 255) || bytes < kPage) return SV_ERR_ARG;
   sv_pool* p = new sv_pool();
   p->base = (uint8_t*)dev_base;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, dev_base) == cudaSuccess && at.type == cudaMemoryTypeHost) {
+    if (!at.devicePointer) {  // pinned but not mapped into the device's address space
+      delete p;
+      return SV_ERR_ARG;
+    }
+    p->host = true;
+    p->base = (uint8_t*)at.devicePointer;
+  } else {
+    cudaGetLastError();
+  }
   p->bytes = bytes / kPage * kPage;
   p->free_runs[0] = p->bytes;
   *out = p;
@@ -500,7 +523,7 @@ int sv_pool_create(void* dev_base, size_t bytes, sv_pool** out) {
 
 int sv_pool_destroy(sv_pool* p) {
   if (!p) return SV_ERR_ARG;
-  if (p->nstates) return SV_ERR_ARG;
+  if (p->nstates || p->used) return SV_ERR_ARG;  // states (or spilled arenas) remain
   delete p;
   return SV_OK;
 }
@@ -610,7 +633,7 @@ int sv_create_ex(sv_pool* pool, int n, int sl, int bl, double eb, int dtype, siz
       delete s;
       return SV_ERR_OOM;
     }
-    s->arena[id] = pool_ptr(pool, s->arena_r[id].off);
+    s->arena[id] = region_ptr(s->arena_r[id]);
   }
   pool->nstates++;
   *out = s;
@@ -801,6 +824,12 @@ int sv_set_chunk(sv_state* s, int chunk) {
   return sv_reset_basis(s, 0);  // the stored streams were coded with the old chunk size
 }
 
+int sv_set_spill_pool(sv_state* s, sv_pool* spill) {
+  if (!s || s->plain || spill == s->pool) return SV_ERR_ARG;
+  s->spill = spill;
+  return SV_OK;
+}
+
 int sv_set_tensor_cores(sv_state* s, int on) {
   if (!s || s->plain) return SV_ERR_ARG;
   s->tensor_cores = on != 0;
@@ -840,6 +869,8 @@ int sv_stats(sv_state* s, sv_stats_t* out) {
   out->blocks_reused = h.last.reused;
   out->replayed_passes = s->replayed;
   out->peak_compressed_bytes = h.peak_bytes;
+  for (int id = 0; id < 2; ++id)
+    if (s->arena_r[id].live && s->arena_r[id].owner != s->pool) out->spill_arena_bytes += s->arena_r[id].bytes;
   return SV_OK;
 }
 
@@ -865,7 +896,7 @@ int sv_block_stream(sv_state* s, uint64_t b, uint8_t* out, size_t cap, size_t* l
   *len = l;
   if (!out) return SV_OK;
   if (cap < l) return SV_ERR_ARG;
-  e = cudaMemcpy(out, s->arena[s->cur] + off, l, cudaMemcpyDeviceToHost);
+  e = cudaMemcpy(out, s->arena[s->cur] + off, l, cudaMemcpyDefault);  // the arena may be host memory
   return cuda_err(e);
 }
 

@@ -46,7 +46,7 @@ class Stats(ctypes.Structure):
         ("blocks_pack", ctypes.c_uint64), ("n_verbatim", ctypes.c_uint64),
         ("n_escape", ctypes.c_uint64), ("norm", ctypes.c_double), ("sigma", ctypes.c_double),
         ("blocks_reused", ctypes.c_uint64), ("replayed_passes", ctypes.c_uint64),
-        ("peak_compressed_bytes", ctypes.c_uint64),
+        ("peak_compressed_bytes", ctypes.c_uint64), ("spill_arena_bytes", ctypes.c_uint64),
     ]
 
     def as_dict(self):
@@ -73,6 +73,7 @@ _SIGS = {
     "sv_set_threads": ([_vp, _i], _i),
     "sv_set_compact": ([_vp, _i], _i),
     "sv_set_tensor_cores": ([_vp, _i], _i),
+    "sv_set_spill_pool": ([_vp, _vp], _i),
     "sv_set_chunk": ([_vp, _i], _i),
     "sv_measure_probs": ([_vp, _vp, _i, _vp], _i),
     "sv_amplitudes": ([_vp, _vp, _sz, _vp], _i),
@@ -96,7 +97,10 @@ _SIGS = {
     "sv_get_pass_timing": ([_vp, _P(_d), _P(_u64), _P(_u64)], _i),
     "sv_version": ([], ctypes.c_char_p),
 }
+_OPTIONAL = {"sv_set_tensor_cores", "sv_set_spill_pool"}  # absent from builds that predate them
 for _name, (_args, _res) in _SIGS.items():
+    if _name in _OPTIONAL and not hasattr(_L, _name):
+        continue
     _f = getattr(_L, _name)
     _f.argtypes = _args
     _f.restype = _res
@@ -116,7 +120,10 @@ class Pool:
     """One caller-owned device buffer (a torch uint8 tensor) the library sub-allocates."""
 
     def __init__(self, nbytes: int, device="cuda"):
-        self.buf = torch.empty(int(nbytes), dtype=torch.uint8, device=device)
+        if device == "host":  # pinned host memory the device addresses: a spill pool
+            self.buf = torch.empty(int(nbytes), dtype=torch.uint8).pin_memory()
+        else:
+            self.buf = torch.empty(int(nbytes), dtype=torch.uint8, device=device)
         h = ctypes.c_void_p()
         _check(_L.sv_pool_create(self.buf.data_ptr(), self.buf.numel(), ctypes.byref(h)), "sv_pool_create")
         self._h = h
@@ -183,6 +190,11 @@ class State:
     def set_chunk(self, chunk: int) -> None:
         """Huffman chunk size of the block format (16, 32, 64); resets the state to |0...0>."""
         _check(_L.sv_set_chunk(self._h, int(chunk)), "sv_set_chunk")
+
+    def set_spill(self, pool: "Pool | None") -> None:
+        """Arenas that do not fit in the state's pool go to `pool` (e.g. Pool(n, "host"))."""
+        _check(_L.sv_set_spill_pool(self._h, pool.handle if pool is not None else None), "sv_set_spill_pool")
+        self.spill_pool = pool
 
     def set_tensor_cores(self, on: bool) -> None:
         """4- and 5-qubit complex128 gates on the tensor cores (default) or the CUDA cores
