@@ -524,27 +524,38 @@ __device__ __forceinline__ void pass_body(const PassArgs& a) {
   }
 }
 
-// The pass kernel without a register cap, and (COMPACT) with one: 64 registers per thread,
-// spilling, so that four 256-thread CTAs fit on an SM.
-// 4- and 5-qubit gates (KM = 32): at most 128 registers, so that the two CTAs per SM that the
-// shared memory admits also fit the register file
+// The pass kernel without a register cap (the compiler picks the count), and (COMPACT) with
+// one: 64 registers per thread, spilling, so that four 256-thread CTAs fit on an SM.
 template <typename Real, int KM>
-__global__ void __launch_bounds__(256, KM > 8 ? 2 : 1) k_pass(const PassArgs a) {
+__global__ void __launch_bounds__(256) k_pass(const PassArgs a) {
   pass_body<Real, KM>(a);
 }
 template <typename Real, int KM>
 __global__ void __launch_bounds__(256, 4) k_pass_c(const PassArgs a) {
   pass_body<Real, KM>(a);
 }
+// 4- and 5-qubit gates: at most 128 registers, so that the two CTAs per SM that the shared
+// memory admits also fit the register file. A kernel of its own: a minimum of one CTA per SM
+// on k_pass lets the compiler take up to 255 registers for the smaller gates too, which
+// halves their resident CTAs.
+template <typename Real>
+__global__ void __launch_bounds__(256, 2) k_pass_big(const PassArgs a) {
+  pass_body<Real, 32>(a);
+}
 
+template <typename Real, int KM, bool COMPACT>
+constexpr auto pass_kernel() {
+  if constexpr (KM > 8) return k_pass_big<Real>;
+  else if constexpr (COMPACT) return k_pass_c<Real, KM>;
+  else return k_pass<Real, KM>;
+}
 
 template <typename Real, int KM, bool COMPACT>
 static cudaError_t launch_pass_k(const PassArgs& a, cudaStream_t st) {
   const Layout L = make_layout(a.b, a.G, (int)sizeof(Real), false, KM > 8);
   static std::atomic<unsigned long long> configured{0};  // devices set up
   cudaError_t ce = once_per_device(configured, [] {
-    if constexpr (COMPACT) return cudaFuncSetAttribute(k_pass_c<Real, KM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    else return cudaFuncSetAttribute(k_pass<Real, KM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    return cudaFuncSetAttribute(pass_kernel<Real, KM, COMPACT>(), cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   });
   if (ce != cudaSuccess) return ce;
   if (L.total > 227 * 1024) return cudaErrorInvalidValue;
@@ -565,8 +576,8 @@ static cudaError_t launch_pass_k(const PassArgs& a, cudaStream_t st) {
       grid = (unsigned long long)sms * per_sm;
   }
   if (grid > 0x7fffffffull) grid = 0x7fffffffull;
-  if constexpr (COMPACT) k_pass_c<Real, KM><<<(unsigned int)grid, T, L.total, st>>>(a);
-  else k_pass<Real, KM><<<(unsigned int)grid, T, L.total, st>>>(a);
+  const auto kern = pass_kernel<Real, KM, COMPACT>();
+  kern<<<(unsigned int)grid, T, L.total, st>>>(a);
   return cudaGetLastError();
 }
 
