@@ -54,14 +54,16 @@ def workload(name: str):
                     basis=x, pool_gb=150.0, threads=256, compact=True,
                     desc="QFT on a random basis state, 34 qubits, complex128, eb 1e-7 abs, slice_log2 24, "
                          "compressed pool capped at 150 GB")
-    if name == "qft26p":
-        # the 34-qubit workload's codec work on a state ncu can capture: amplitudes 2^-13 at
-        # eb 1.6e-6 have the codes of amplitudes 2^-17 at eb 1e-7 (|q| about 38), same launch shape
-        n = 26
-        return dict(name="qft26p", n=n, eb=1.6e-6, slice_log2=24, block_log2=11, dtype=2, gates=C.qft(n),
+    if name in ("qft26p", "qft28p"):
+        # the 34-qubit workload's codec work on a state ncu can capture: amplitudes 2^-n/2 at
+        # eb 1e-7 2^((34 - n) / 2) have the codes of amplitudes 2^-17 at eb 1e-7 (|q| about 38),
+        # same launch shape; two sizes show how a launch's DRAM traffic grows with the state
+        n = int(name[3:5])
+        eb = 1e-7 * 2.0 ** ((34 - n) / 2)
+        return dict(name=name, n=n, eb=eb, slice_log2=24, block_log2=11, dtype=2, gates=C.qft(n),
                     basis=C.seeded_index(0, n), pool_gb=8.0, threads=256, compact=True,
-                    desc="QFT on a random basis state, 26 qubits, complex128, eb 1.6e-6 abs (the codes of the "
-                         "34-qubit workload), slice_log2 24")
+                    desc="QFT on a random basis state, %d qubits, complex128, eb %.3g abs (the codes of the "
+                         "34-qubit workload), slice_log2 24" % (n, eb))
     if name == "qft12":
         n = 12
         return dict(name="qft12", n=n, eb=1e-6, slice_log2=8, block_log2=8, dtype=2, gates=C.qft(n),
@@ -828,7 +830,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="qft34", choices=["qft34", "qft26p", "grover20", "qft12", "random30"])
+    ap.add_argument("--workload", default="qft34", choices=["qft34", "qft26p", "qft28p", "grover20", "qft12", "random30"])
     ap.add_argument("--block-log2", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0, help="CTA size of the fused pass (0: tuned/default)")
     ap.add_argument("--compact", action="store_true", help="register-capped build of the fused pass")

@@ -215,8 +215,8 @@ int sv_stats(sv_state* s, sv_stats_t* out);
 int sv_set_threads(sv_state* s, int threads);
 
 /* Select (on != 0) the register-capped build of the fused pass for 1- and 2-qubit gates
- * (64 registers per thread, so that four 256-thread CTAs fit on an SM; larger gates keep the
- * default build). An autotuning knob with no counterpart in the paper; results do not
+ * (1-qubit gates: 64 registers per thread, so that four 256-thread CTAs fit on an SM; 2-qubit
+ * gates: 85, three CTAs; larger gates keep the default build). An autotuning knob with no counterpart in the paper; results do not
  * depend on it. SV_ERR_ARG for a plain state. Batches ignore it. */
 int sv_set_compact(sv_state* s, int on);
 

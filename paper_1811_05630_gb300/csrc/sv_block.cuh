@@ -856,8 +856,8 @@ struct Worker {
 
 // Two-queue Huffman merge over D >= 2 leaves sorted by (frequency, symbol) in keys (frequency
 // in the upper 16 bits): each step joins the two lightest queue heads, the leaf queue first on
-// equal weight. Writes wint[k] (internal node k = node D + k) and parent[v] for every node but
-// the root (2D - 2).
+// equal weight. Writes parent[v] for every node but the root (2D - 2), and wint[k] (internal
+// node k = node D + k) for the nodes formed before the last leaf is consumed.
 //
 // In rounds rather than D - 1 serial steps. The steps consume the nodes in the order of S, the
 // merge of the leaf list with the internal-node list (leaves first on equal weight), and
@@ -867,7 +867,8 @@ struct Worker {
 // weight <= thr therefore precedes every unformed one (a leaf wins a tie; a known internal
 // node was formed earlier), so one round places all of them at once, each at its merge
 // position, and forms the internal nodes their pairs complete. thr at least doubles every
-// round, so a block (total weight < 2^16) needs at most 17 rounds. One warp runs the rounds
+// round, so a block (total weight < 2^16) needs at most 17 rounds; once the last leaf is
+// placed the remaining pairs are fixed by position and need no round. One warp runs the rounds
 // (warp votes and warp barriers only); the CTA waits once, after it. sw, sid: scratch for S
 // (weights and node ids, 2D - 2 entries each).
 __device__ inline void huffman_merge(const uint32_t* keys, int D, uint32_t* wint, uint16_t* parent,
@@ -877,6 +878,14 @@ __device__ inline void huffman_merge(const uint32_t* keys, int D, uint32_t* wint
     int m = 0, lp = 0, ip = 0;  // S entries placed, leaves and internal nodes consumed (uniform)
     while (m < 2 * D - 2) {
       const int nk = m >> 1;  // internal nodes formed
+      if (lp == D) {
+        // every leaf is placed: the rest of S is the internal-node queue in order, so the
+        // entry at position p >= m is internal node p - D (node id p), and every pair
+        // (2k, 2k + 1) from 2 nk on forms internal node k without any weight being needed
+        for (int p = 2 * nk + lane; p < 2 * D - 2; p += 32) parent[p < m ? sid[p] : p] = (uint16_t)(D + (p >> 1));
+        __syncwarp();
+        break;
+      }
       uint32_t v0 = 0xFFFFFFFFu;
       if (lp < D) v0 = keys[lp] >> 16;
       if (ip < nk && wint[ip] < v0) v0 = wint[ip];

@@ -353,60 +353,74 @@ __device__ __forceinline__ void pass_group(Worker<Real>& w, const PassArgs& a, c
     }
     if constexpr (KM <= 8) {
     const int ntup = B >> a.nlow;
+    // the gate's scalars in registers for the whole loop (the code stores below would
+    // otherwise make the compiler read them again for every tuple)
+    int gF = -1, gqsafe = 0, gdiag = 0, greal = 0;
+    long long gmargin = 0;
+    int32_t gidhi = 0, gidlo = 0;
+    if (kFast) {
+      gF = fg->F;
+      gqsafe = fg->qsafe;
+      gdiag = fg->diag;
+      greal = fg->real;
+      gmargin = fg->margin;
+      gidhi = fg->idhi;
+      gidlo = fg->idlo;
+    }
+    const unsigned long long blk0 = blk_of(0);
     for (int u = threadIdx.x; u < ntup; u += blockDim.x) {
       unsigned long long o = (unsigned long long)u;
       for (int l = 0; l < a.nlow; ++l) o = insert_zero_bit(o, a.low_t[l]);
-      const unsigned long long gidx = (blk_of(0) << a.b) | o;
+      const unsigned long long gidx = (blk0 << a.b) | o;
       const bool ctrl = a.apply_gate && ((gidx & a.cmask) == a.cmask);
       const int bp = 2 * (int)o;
-      if (kFast && fg->F >= 0) {
+      if (kFast && gF >= 0) {
+        // member m's values sit at bp + pos_delta[m] (+1) of the group's code array, whose
+        // blocks are contiguous
         int32_t qv[2 * KM];
-        int gq[KM], jq[KM];
         bool sentinel = false;
   #pragma unroll
         for (int mm = 0; mm < KM; ++mm)
           if (mm < a.K) {
             const int p = bp + a.pos_delta[mm];
-            gq[mm] = p >> (a.b + 1);
-            jq[mm] = p & (L.nv - 1);
             qv[2 * mm] = w.q[p];
             qv[2 * mm + 1] = w.q[p + 1];
             sentinel |= qv[2 * mm] == kSentinel || qv[2 * mm + 1] == kSentinel;
           }
         if (!sentinel) {
-          const int F = fg->F;
-          const long long margin = fg->margin;
-          int32_t out[2 * KM];
-          unsigned int exact_mask = 0;
+          // every input of the tuple is in registers: each output is stored as soon as it is
+          // known (the tuples' positions are disjoint)
   #pragma unroll
           for (int jj = 0; jj < KM; ++jj)
             if (jj < a.K) {
+              const int pj = bp + a.pos_delta[jj];
   #pragma unroll
               for (int p = 0; p < 2; ++p) {
+                int32_t oc = 0;
+                bool done = false;
                 // outputs that are +-1 times one input: exact without arithmetic when small
                 const int ssrc = ctrl ? fg->ssrc[jj][p] : 2 * jj + p;
-                bool done = false;
                 if (ssrc >= 0) {
                   int32_t qq = 0;
   #pragma unroll
                   for (int e = 0; e < 2 * KM; ++e)
                     if (e == ssrc) qq = qv[e];
-                  if ((qq < 0 ? -qq : qq) <= fg->qsafe) {
-                    out[2 * jj + p] = (ctrl && fg->ssgn[jj][p] < 0) ? -qq : qq;
+                  if ((qq < 0 ? -qq : qq) <= gqsafe) {
+                    oc = (ctrl && fg->ssgn[jj][p] < 0) ? -qq : qq;
                     done = true;
                   }
                 }
                 if (!done) {
                   long long sh = 0, sl = 0;
-                  if (ctrl && fg->diag) {
-    #pragma unroll
+                  if (ctrl && gdiag) {
+  #pragma unroll
                     for (int c = 0; c < 2; ++c) {
                       const long long qq = qv[2 * jj + c];
                       sh += qq * fg->chi[jj][p][jj][c];
                       sl += (qq * fg->clo[jj][p][jj][c]) >> 4;
                     }
-                  } else if (ctrl && fg->real) {  // real matrix: the cross terms are exactly 0
-    #pragma unroll
+                  } else if (ctrl && greal) {  // real matrix: the cross terms are exactly 0
+  #pragma unroll
                     for (int m = 0; m < KM; ++m)
                       if (m < a.K) {
                         const long long qq = qv[2 * m + p];
@@ -414,10 +428,10 @@ __device__ __forceinline__ void pass_group(Worker<Real>& w, const PassArgs& a, c
                         sl += (qq * fg->clo[jj][p][m][p]) >> 4;
                       }
                   } else if (ctrl) {
-    #pragma unroll
+  #pragma unroll
                     for (int m = 0; m < KM; ++m)
                       if (m < a.K) {
-    #pragma unroll
+  #pragma unroll
                         for (int c = 0; c < 2; ++c) {
                           const long long qq = qv[2 * m + c];
                           sh += qq * fg->chi[jj][p][m][c];
@@ -426,27 +440,15 @@ __device__ __forceinline__ void pass_group(Worker<Real>& w, const PassArgs& a, c
                       }
                   } else {
                     const long long qq = qv[2 * jj + p];
-                    sh = qq * fg->idhi;
-                    sl = (qq * fg->idlo) >> 4;
+                    sh = qq * gidhi;
+                    sl = (qq * gidlo) >> 4;
                   }
-                  if (!fast_round(sh + (sl >> 27), F, margin, &out[2 * jj + p])) exact_mask |= 1u << (2 * jj + p);
+                  done = fast_round(sh + (sl >> 27), gF, gmargin, &oc);
                 }
-              }
-            }
-          double zx[2 * KM];
-          if (exact_mask) {
-  #pragma unroll
-            for (int e = 0; e < 2 * KM; ++e)
-              if ((exact_mask >> e) & 1u) zx[e] = exact_component<KM>(a, sigma, qv, e >> 1, e & 1, ctrl);
-          }
-  #pragma unroll
-          for (int mm = 0; mm < KM; ++mm)
-            if (mm < a.K) {
-  #pragma unroll
-              for (int p = 0; p < 2; ++p) {
-                const int e = 2 * mm + p;
-                if ((exact_mask >> e) & 1u) w.put_value(gq[mm], jq[mm] + p, (Real)zx[e]);
-                else w.q[gq[mm] * L.nv + jq[mm] + p] = out[e];
+                if (done) w.q[pj + p] = oc;
+                else  // near a rounding tie or at the code range: the exact step chain
+                  w.put_value(pj >> (w.b + 1), (pj & (L.nv - 1)) + p,
+                              (Real)exact_component<KM>(a, sigma, qv, jj, p, ctrl));
               }
             }
           continue;
@@ -525,13 +527,20 @@ __device__ __forceinline__ void pass_body(const PassArgs& a) {
 }
 
 // The pass kernel without a register cap (the compiler picks the count), and (COMPACT) with
-// one: 64 registers per thread, spilling, so that four 256-thread CTAs fit on an SM.
+// one. 1-qubit gates (one block per CTA, 55 KB of shared memory at 2048-amplitude blocks): 64
+// registers per thread, spilling, so that four 256-thread CTAs fit on an SM. 2-qubit gates
+// (up to two coupled blocks, 75 KB): 85 registers, so that the three CTAs the shared memory
+// admits also fit the register file.
 template <typename Real, int KM>
 __global__ void __launch_bounds__(256) k_pass(const PassArgs a) {
   pass_body<Real, KM>(a);
 }
 template <typename Real, int KM>
 __global__ void __launch_bounds__(256, 4) k_pass_c(const PassArgs a) {
+  pass_body<Real, KM>(a);
+}
+template <typename Real, int KM>
+__global__ void __launch_bounds__(256, 3) k_pass_c3(const PassArgs a) {
   pass_body<Real, KM>(a);
 }
 // 4- and 5-qubit gates: at most 128 registers, so that the two CTAs per SM that the shared
@@ -546,6 +555,7 @@ __global__ void __launch_bounds__(256, 2) k_pass_big(const PassArgs a) {
 template <typename Real, int KM, bool COMPACT>
 constexpr auto pass_kernel() {
   if constexpr (KM > 8) return k_pass_big<Real>;
+  else if constexpr (COMPACT && KM == 4) return k_pass_c3<Real, KM>;
   else if constexpr (COMPACT) return k_pass_c<Real, KM>;
   else return k_pass<Real, KM>;
 }

@@ -52,7 +52,7 @@ def test_arenas_in_host_memory_bit_exact(sv, dtype):
 
 
 def test_spill_pool_arguments(sv):
-    dev = sv.Pool(8 << 20)
+    dev = sv.Pool(16 << 20)  # pages for a compressed state and a plain one
     st = sv.State(dev, 10, 10, 1e-6, oracle.C128, block_log2=6)
     try:
         with pytest.raises(sv.SvError) as e:
