@@ -711,6 +711,34 @@ struct Worker {
     return (uint32_t)L.hs;
   }
 
+  // Add `cnt` occurrences of symbol `sym` to the histogram's hash table, unless the block
+  // already has more distinct symbols than Huffman mode takes (m->D then exceeds kHuffMaxD
+  // and the block is packed).
+  __device__ __forceinline__ void hash_add(uint32_t sym, uint32_t cnt) {
+    if (*(volatile int*)&m->D > kHuffMaxD) return;
+    uint32_t hslot = hash_sym(sym) & (uint32_t)(L.hs - 1);
+    for (int probe = 0; probe < L.hs; ++probe) {
+      const uint32_t k = hkey[hslot];
+      if (k == sym) {
+        atomicAdd(&hval[hslot], cnt);
+        return;
+      }
+      if (k == kEmpty) {
+        const uint32_t old = atomicCAS(&hkey[hslot], kEmpty, sym);
+        if (old == kEmpty) {
+          atomicAdd(&m->D, 1);
+          atomicAdd(&hval[hslot], cnt);
+          return;
+        }
+        if (old == sym) {
+          atomicAdd(&hval[hslot], cnt);
+          return;
+        }
+      }
+      hslot = (hslot + 1) & (uint32_t)(L.hs - 1);
+    }
+  }
+
   // Quantize one result into slot g position j (Compress(S), first step).
   __device__ __forceinline__ void put_value(int g, int j, Real v) {
     int32_t c;
@@ -863,8 +891,8 @@ struct Worker {
 // merge of the leaf list with the internal-node list (leaves first on equal weight), and
 // internal node k joins S[2k] and S[2k + 1]. With m entries of S placed, the internal nodes
 // 0 .. m/2 - 1 are known, and every node not yet formed weighs at least thr = S[m-1] + v0
-// (m odd) or 2 v0 (m even), v0 the lightest node available now. Every available node of
-// weight <= thr therefore precedes every unformed one (a leaf wins a tie; a known internal
+// (m odd) or v0 + v1 (m even), v0 <= v1 the two lightest nodes available now. Every available
+// node of weight <= thr therefore precedes every unformed one (a leaf wins a tie; a known internal
 // node was formed earlier), so one round places all of them at once, each at its merge
 // position, and forms the internal nodes their pairs complete. thr at least doubles every
 // round, so a block (total weight < 2^16) needs at most 17 rounds; once the last leaf is
@@ -886,21 +914,37 @@ __device__ inline void huffman_merge(const uint32_t* keys, int D, uint32_t* wint
         __syncwarp();
         break;
       }
-      uint32_t v0 = 0xFFFFFFFFu;
-      if (lp < D) v0 = keys[lp] >> 16;
-      if (ip < nk && wint[ip] < v0) v0 = wint[ip];
-      const uint32_t thr = (m & 1) ? sw[m - 1] + v0 : 2u * v0;
-      // available nodes at or below thr (each list is sorted, so they form prefixes)
-      int cl = 0, ci = 0;
-      for (int t0 = 0; t0 < D - lp; t0 += 32) {
-        const unsigned v = __ballot_sync(0xffffffffu, t0 + lane < D - lp && (keys[lp + t0 + lane] >> 16) <= thr);
-        cl += __popc(v);
-        if (v != 0xffffffffu) break;
+      // the next 32 nodes of each queue (one load each) and the pending entry S[m - 1]
+      constexpr unsigned kAll = 0xffffffffu;
+      const uint32_t kl = lp + lane < D ? keys[lp + lane] >> 16 : 0xFFFFFFFFu;
+      const uint32_t wl = ip + lane < nk ? wint[ip + lane] : 0xFFFFFFFFu;
+      const uint32_t pend = (m & 1) ? sw[m - 1] : 0u;
+      const uint32_t l0 = __shfl_sync(kAll, kl, 0), l1 = __shfl_sync(kAll, kl, 1);
+      const uint32_t i0 = __shfl_sync(kAll, wl, 0), i1 = __shfl_sync(kAll, wl, 1);
+      // v0 <= v1: the two lightest available nodes (a leaf first on equal weight). The next
+      // internal node joins S[m - 1] and v0 (m odd) or v0 and v1 (m even), and no node
+      // formed after it is lighter: thr bounds every node not yet formed from below.
+      uint32_t v0, v1;
+      if (l0 <= i0) {
+        v0 = l0;
+        v1 = l1 < i0 ? l1 : i0;
+      } else {
+        v0 = i0;
+        v1 = i1 < l0 ? i1 : l0;
       }
-      for (int t0 = 0; t0 < nk - ip; t0 += 32) {
-        const unsigned v = __ballot_sync(0xffffffffu, t0 + lane < nk - ip && wint[ip + t0 + lane] <= thr);
-        ci += __popc(v);
-        if (v != 0xffffffffu) break;
+      const uint32_t thr = (m & 1) ? pend + v0 : (v1 != 0xFFFFFFFFu ? v0 + v1 : 2u * v0);
+      // available nodes at or below thr (each list is sorted, so they form prefixes)
+      unsigned vb = __ballot_sync(kAll, kl <= thr);
+      int cl = __popc(vb);
+      for (int t0 = 32; vb == kAll && t0 < D - lp; t0 += 32) {
+        vb = __ballot_sync(kAll, t0 + lane < D - lp && (keys[lp + t0 + lane] >> 16) <= thr);
+        cl += __popc(vb);
+      }
+      vb = __ballot_sync(kAll, wl <= thr);
+      int ci = __popc(vb);
+      for (int t0 = 32; vb == kAll && t0 < nk - ip; t0 += 32) {
+        vb = __ballot_sync(kAll, t0 + lane < nk - ip && wint[ip + t0 + lane] <= thr);
+        ci += __popc(vb);
       }
       // merge positions: a leaf follows the internal nodes lighter than it, an internal node
       // follows the leaves not heavier than it
@@ -1016,12 +1060,20 @@ __device__ __forceinline__ void Worker<Real>::encode(int g, unsigned long long b
   const bool big = !kMask && nverb > kVmax;
   const int C = nv / kc;
   // ---- pass 1: statistics and the symbol histogram over this thread's values ----
-  // (hash table; runs of equal symbols merged before an insert; inserts stop once the block
-  // has more distinct symbols than Huffman mode takes)
+  // Symbols near 32768 (small deltas) are counted in direct bins in the stage buffer, which
+  // is idle until the stream image is assembled; the others go to the hash table (runs of
+  // equal symbols merged before an insert; inserts stop once the block has more distinct
+  // symbols than Huffman mode takes). After the pass every nonzero bin enters the hash table
+  // with its count, so the codebook build and the code lookup see one table.
+  uint32_t* bins = stage;
+  int nbin = kBinsMax;
+  while (nbin > 32 && (uint32_t)nbin * 4u > L.stage_bytes) nbin >>= 1;
+  const uint32_t bin0 = 32768u - (uint32_t)(nbin >> 1);  // symbol of bin 0
   for (int i = tid; i < L.hs; i += T) {
     hkey[i] = kEmpty;
     hval[i] = 0;
   }
+  for (int i = tid; i < nbin; i += T) bins[i] = 0;
   if (tid == 0) {
     m->D = 0;
     m->cnt = 0;
@@ -1064,34 +1116,18 @@ __device__ __forceinline__ void Worker<Real>::encode(int g, unsigned long long b
         run++;
         continue;
       }
-      if (run && *(volatile int*)&m->D <= kHuffMaxD) {
-        uint32_t hslot = hash_sym(run_sym) & (uint32_t)(L.hs - 1);
-        for (int probe = 0; probe < L.hs; ++probe) {
-          const uint32_t k = hkey[hslot];
-          if (k == run_sym) {
-            atomicAdd(&hval[hslot], run);
-            break;
-          }
-          if (k == kEmpty) {
-            const uint32_t old = atomicCAS(&hkey[hslot], kEmpty, run_sym);
-            if (old == kEmpty) {
-              atomicAdd(&m->D, 1);
-              atomicAdd(&hval[hslot], run);
-              break;
-            }
-            if (old == run_sym) {
-              atomicAdd(&hval[hslot], run);
-              break;
-            }
-          }
-          hslot = (hslot + 1) & (uint32_t)(L.hs - 1);
-        }
+      if (run) {
+        if (run_sym - bin0 < (uint32_t)nbin) atomicAdd(&bins[run_sym - bin0], run);
+        else hash_add(run_sym, run);
       }
       run_sym = sym;
       run = 1;
     }
   }
-  block_reduce_stats(bs, (BlkStats*)m->red);  // syncs: the histogram is complete after it
+  block_reduce_stats(bs, (BlkStats*)m->red);  // syncs: every value is counted after it
+  for (int i = tid; i < nbin; i += T)
+    if (bins[i]) hash_add(bin0 + (uint32_t)i, bins[i]);
+  __syncthreads();
   const bool is_const = bs.cst && nverb_raw == 0;
   const unsigned long long Sh = bs.sqh, Sl = bs.sql;
   uint32_t amax = bs.amax;

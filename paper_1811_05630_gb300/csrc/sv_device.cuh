@@ -28,6 +28,7 @@ constexpr int kRadius = 32767;
 constexpr int kChunkDefault = 32, kChunkMin = 16;
 constexpr int kHuffMaxD = 256;        // more distinct symbols: PACK
 constexpr int kHashSlots = 512;       // >= 2 * kHuffMaxD
+constexpr int kBinsMax = 2048;        // direct histogram bins (symbols 32768 +- 1024)
 constexpr int kLutBits = 10;          // decode table width
 constexpr int kVmax = 128;            // GPU limit: verbatim values per block
 constexpr int kModeConst = 0, kModeHuff = 1, kModePack = 2;
