@@ -49,9 +49,11 @@ def workload(name: str):
         n = 34
         x = C.seeded_index(0, n)
         # the launch shape the tuner picked on QFT dense stages (tuning at 34 qubits would take
-        # minutes per candidate): 2048-amplitude blocks, 256 threads, register-capped build
+        # minutes per candidate): 2048-amplitude blocks, 256 threads, register-capped build;
+        # 16-symbol Huffman chunks (every thread decodes: 3.03 ms against 3.33 ms per pass of
+        # chunk 32 on the 26-qubit stand-in's window, whose final size is the same)
         return dict(name="qft34", n=n, eb=1e-7, slice_log2=24, block_log2=11, dtype=2, gates=C.qft(n),
-                    basis=x, pool_gb=150.0, threads=256, compact=True,
+                    basis=x, pool_gb=150.0, threads=256, compact=True, chunk=16,
                     desc="QFT on a random basis state, 34 qubits, complex128, eb 1e-7 abs, slice_log2 24, "
                          "compressed pool capped at 150 GB")
     if name in ("qft26p", "qft28p"):
@@ -61,7 +63,7 @@ def workload(name: str):
         n = int(name[3:5])
         eb = 1e-7 * 2.0 ** ((34 - n) / 2)
         return dict(name=name, n=n, eb=eb, slice_log2=24, block_log2=11, dtype=2, gates=C.qft(n),
-                    basis=C.seeded_index(0, n), pool_gb=8.0, threads=256, compact=True,
+                    basis=C.seeded_index(0, n), pool_gb=8.0, threads=256, compact=True, chunk=16,
                     desc="QFT on a random basis state, %d qubits, complex128, eb %.3g abs (the codes of the "
                          "34-qubit workload), slice_log2 24" % (n, eb))
     if name == "qft12":
@@ -185,11 +187,12 @@ def source_digest() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(workload: str, block_log2: int, threads: int, compact: bool, window: str = ""):
+def recorded_traffic(workload: str, block_log2: int, threads: int, compact: bool, window: str = "",
+                     chunk: int = 32):
     """DRAM bytes per fused-pass launch from the committed ncu summary of this workload, when
     it was taken on these exact kernel sources, this launch configuration (block size, CTA
-    size, build) and the same window of passes: (bytes, description of the captured
-    launches), else (None, why not)."""
+    size, build, Huffman chunk) and the same window of passes: (bytes, description of the
+    captured launches), else (None, why not)."""
     path = os.path.join(ROOT, "profiles", "k_pass_%s.md" % workload)
     why = "no ncu capture recorded for this workload"
     try:
@@ -200,8 +203,8 @@ def recorded_traffic(workload: str, block_log2: int, threads: int, compact: bool
                     if kv.get("digest") != source_digest():
                         why = "kernel sources changed since the ncu capture"
                         continue
-                    if (int(kv["block_log2"]), int(kv["threads"]), bool(int(kv["compact"]))) != (
-                            block_log2, threads, bool(compact)):
+                    if (int(kv["block_log2"]), int(kv["threads"]), bool(int(kv["compact"])),
+                            int(kv.get("chunk", "32"))) != (block_log2, threads, bool(compact), chunk):
                         why = "no ncu capture at this launch configuration"
                         continue
                     if kv.get("window", "") != window:
@@ -285,7 +288,8 @@ def _oracle_at(sw, w0):
 
     n = sw["n"]
     ps = oracle.PlainSim(n, sw["dtype"], sw["basis"]).run(sw["gates"][:w0])
-    cs = oracle.CompressedSim(n, min(sw["slice_log2"], n), sw["block_log2"], sw["dtype"], sw["eb"], 0)
+    cs = oracle.CompressedSim(n, min(sw["slice_log2"], n), sw["block_log2"], sw["dtype"], sw["eb"], 0,
+                              chunk=sw.get("chunk", 32))
     cs.load(ps.state)
     return cs
 
@@ -390,7 +394,7 @@ def run_ours(args, rank, world, dist):
 
         i0t = start_of_dense_stage(wl)
         tuned = tune.best_config(n, wl["dtype"], wl["eb"], wl["name"], gates[:i0t], gates[i0t:i0t + 200],
-                                 basis=wl["basis"], use_cache=False)
+                                 basis=wl["basis"], use_cache=False, chunks=(16, 32))
         wl["block_log2"] = tuned["block_log2"]
         wl["threads"] = tuned["threads"]
         wl["compact"] = tuned["compact"]
@@ -516,7 +520,7 @@ def run_ours(args, rank, world, dist):
         # the default CTA size is one thread per 32-value decode chunk, 32 to 256 threads
         eff_threads = int(wl.get("threads") or min(256, max(32, (2 << b) // 32)))
         traffic, traffic_src = recorded_traffic(wl["name"], b, eff_threads, bool(wl.get("compact")),
-                                                window="%d-%d" % (t0, t1))
+                                                window="%d-%d" % (t0, t1), chunk=wl.get("chunk", 32))
         roof = {"bound": "hbm", "achieved": achieved, "peak": pk.get("hbm_gbs"), "unit": "GB/s",
                 "frac": achieved / pk.get("hbm_gbs", 1.0), "traffic": traffic,
                 "traffic_source": traffic_src, "source_digest": source_digest(),

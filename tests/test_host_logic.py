@@ -366,6 +366,8 @@ def test_traffic_record_needs_matching_sources_and_shape(monkeypatch, tmp_path):
     assert bench.recorded_traffic("demo", 11, 256, True, window="586-606") == (123.0, "x y")
     assert bench.recorded_traffic("demo", 10, 256, True, window="586-606")[0] is None
     assert bench.recorded_traffic("demo", 11, 256, False, window="586-606")[0] is None
+    # a line without a chunk size describes the default 32-symbol chunks only
+    assert bench.recorded_traffic("demo", 11, 256, True, window="586-606", chunk=16)[0] is None
     # a capture of another window of passes does not describe this run's launches
     assert bench.recorded_traffic("demo", 11, 256, True, window="25-45") == (
         None, "no ncu capture of this window of passes")
@@ -373,6 +375,11 @@ def test_traffic_record_needs_matching_sources_and_shape(monkeypatch, tmp_path):
     assert bench.recorded_traffic("demo", 11, 256, True, window="586-606") == (
         None, "kernel sources changed since the ncu capture")
     assert bench.recorded_traffic("other", 11, 256, True, window="586-606")[0] is None
+    (prof / "k_pass_demo16.md").write_text(
+        "TRAFFIC digest=def block_log2=11 threads=256 compact=1 chunk=16 window=586-606 bytes_per_launch=7 "
+        "launches=z\n")
+    assert bench.recorded_traffic("demo16", 11, 256, True, window="586-606", chunk=16) == (7.0, "z")
+    assert bench.recorded_traffic("demo16", 11, 256, True, window="586-606")[0] is None
 
 
 def test_clock_summary_reads_throttle_reasons():
