@@ -21,6 +21,7 @@ import argparse
 import json
 import math
 import os
+import re
 import subprocess
 import sys
 import threading
@@ -56,7 +57,7 @@ def workload(name: str):
                     basis=x, pool_gb=150.0, threads=256, compact=True, chunk=16,
                     desc="QFT on a random basis state, 34 qubits, complex128, eb 1e-7 abs, slice_log2 24, "
                          "compressed pool capped at 150 GB")
-    if name in ("qft26p", "qft28p"):
+    if name in ("qft26p", "qft28p", "qft30p"):
         # the 34-qubit workload's codec work on a state ncu can capture: amplitudes 2^-n/2 at
         # eb 1e-7 2^((34 - n) / 2) have the codes of amplitudes 2^-17 at eb 1e-7 (|q| about 38),
         # same launch shape; two sizes show how a launch's DRAM traffic grows with the state
@@ -170,7 +171,8 @@ class ClockSampler:
 
 
 # the device-code sources of the fused pass (host-side files do not change what it moves)
-KERNEL_SOURCES = ("sv_block.cuh", "sv_device.cuh", "sv_pass.cuh", "sv_pass_compact.cu", "sv_kernels.cu")
+KERNEL_SOURCES = ("sv_block.cuh", "sv_device.cuh", "sv_pass.cuh", "sv_pass_big.cuh", "sv_pass_tc.cuh", "sv_tc.cuh",
+                  "sv_pass_compact.cu", "sv_kernels.cu")
 
 
 def source_digest() -> str:
@@ -524,8 +526,8 @@ def run_ours(args, rank, world, dist):
         roof = {"bound": "hbm", "achieved": achieved, "peak": pk.get("hbm_gbs"), "unit": "GB/s",
                 "frac": achieved / pk.get("hbm_gbs", 1.0), "traffic": traffic,
                 "traffic_source": traffic_src, "source_digest": source_digest(),
-                "kernel": "k_pass_c (fused pass, register-capped build)" if wl.get("compact")
-                else "k_pass (fused pass)", "kernel_ms_per_launch": kern_ms / max(npass, 1),
+                "kernel": "k_pass_c / k_pass_c3 (fused pass, register-capped builds for 1- and 2-qubit "
+                          "gates)" if wl.get("compact") else "k_pass (fused pass)", "kernel_ms_per_launch": kern_ms / max(npass, 1),
                 "alg_bytes_per_launch": alg_bytes / max(npass, 1), "launches": npass,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy bandwidth)"
                 if "fallback" not in pk else "fallback 6.8 TB/s"}
@@ -643,9 +645,12 @@ def run_full_circuit(args):
     if args.block_log2:
         wl["block_log2"] = args.block_log2
     if args.eb:
+        wl["desc"] = re.sub(r"eb [0-9.eE+-]+", "eb %.3g" % args.eb, wl["desc"], count=1)
         wl["eb"] = args.eb
     if args.dtype:
         wl["dtype"] = {"c128": 2, "c64": 1}[args.dtype]
+        if args.dtype == "c64":
+            wl["desc"] = wl["desc"].replace("complex128", "complex64")
     n, gates = wl["n"], wl["gates"]
     unfused = len(gates)
     if args.fuse:
@@ -834,7 +839,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="qft34", choices=["qft34", "qft26p", "qft28p", "grover20", "qft12", "random30"])
+    ap.add_argument("--workload", default="qft34", choices=["qft34", "qft26p", "qft28p", "qft30p", "grover20", "qft12", "random30"])
     ap.add_argument("--block-log2", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0, help="CTA size of the fused pass (0: tuned/default)")
     ap.add_argument("--compact", action="store_true", help="register-capped build of the fused pass")
