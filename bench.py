@@ -667,6 +667,8 @@ def run_full_circuit(args):
     if args.threads:
         st.set_threads(args.threads)
     st.set_compact(args.compact)
+    if not args.tensor_cores:
+        st.set_tensor_cores(False)
     if args.chunk and args.chunk != 32:
         st.set_chunk(args.chunk)
     st.reset_basis(wl["basis"])
@@ -706,6 +708,7 @@ def run_full_circuit(args):
         "block_log2": wl["block_log2"], "threads_per_cta": args.threads or "default",
         "register_capped_build": args.compact, "huffman_chunk": args.chunk or 32,
         "gates": unfused, "passes": len(gates), "fused": bool(args.fuse),
+        "tensor_cores": bool(args.tensor_cores) and wl["dtype"] == 2,
         "blocks_reused_fraction": reused / (len(gates) * stt["n_blocks"]),
         "replayed_passes": stt["replayed_passes"],
         "amp_updates_per_s_wall": (1 << n) * unfused / wall,
@@ -860,6 +863,8 @@ def main():
                     help="full-circuit mode: a pinned host-memory spill pool (GB) for arenas beyond the device pool")
     ap.add_argument("--profile-window", action="store_true",
                     help="bracket the timed passes with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
+    ap.add_argument("--no-tensor-cores", dest="tensor_cores", action="store_false",
+                    help="full-circuit mode: 4- and 5-qubit gates on the CUDA cores only")
     ap.add_argument("--fuse", action="store_true",
                     help="full-circuit mode: fuse the circuit into dense gates of up to 5 qubits")
     ap.add_argument("--serve", action="store_true", help="serve the mixed request stream")

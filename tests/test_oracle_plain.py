@@ -77,15 +77,16 @@ def random_unitary(rng, d):
     return q * (np.diag(r) / np.abs(np.diag(r)))
 
 
-@pytest.mark.parametrize("n", [3, 5, 6])
+@pytest.mark.parametrize("n", [3, 5, 6, 7])
 def test_dense_bruteforce(n):
+    # gates on up to five targets (2^k x 2^k matrices, k <= 5), with controls
     rng = np.random.default_rng(100 + n)
     v = rng.standard_normal(1 << n) + 1j * rng.standard_normal(1 << n)
     v /= np.linalg.norm(v)
     sim = oracle.PlainSim(n, oracle.C128, state=v)
     ref = v.copy()
     for _ in range(25):
-        k = int(rng.integers(1, min(3, n - 1) + 1))
+        k = int(rng.integers(1, min(5, n - 1) + 1))
         qs = rng.permutation(n)
         targets = tuple(int(q) for q in qs[:k])
         nc = int(rng.integers(0, n - k + 1))
