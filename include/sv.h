@@ -309,6 +309,16 @@ int sv_codec_compress_static(const void* values, uint64_t nblocks, int block_log
 int sv_set_pass_timing(sv_state* s, int on);
 int sv_get_pass_timing(sv_state* s, double* kernel_ms, uint64_t* passes, uint64_t* bytes);
 
+/* Self-check of the bounded device wait (failure detection; no counterpart in the paper).
+ * The tensor-core pass waits for its matrix multiplies on an mbarrier and gives up after a
+ * bounded number of polls, recording a timeout that the next sv_sync returns as
+ * SV_ERR_TIMEOUT instead of hanging. This call runs that wait on an mbarrier nothing arrives
+ * on, polling `polls` times (1 <= polls <= 2^24), on `stream` (a cudaStream_t; NULL: the
+ * legacy default stream), synchronizes the stream and sets *timed_out to 1 when the wait gave
+ * up (the expected result) and 0 when the phase completed. The context stays usable.
+ * SV_ERR_ARG for a NULL output or polls out of range; SV_ERR_CUDA if a CUDA call failed. */
+int sv_check_bounded_wait(long long polls, void* stream, int* timed_out);
+
 /* Library version string and the sm architecture it was built for. */
 const char* sv_version(void);
 

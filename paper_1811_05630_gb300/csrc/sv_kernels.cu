@@ -7,6 +7,7 @@
 //   k_codec_*         the block codec on its own (Sec. II), same device code as k_pass
 //   k_read_blocks     decoded amplitudes for measurements
 //   k_plain_*         the plain (uncompressed) full amplitude-vector update (Sec. I)
+#include "../../include/sv.h"
 #include "sv_internal.h"
 #include "sv_pass.cuh"
 
@@ -746,4 +747,36 @@ cudaError_t launch_plain_read(const void* psi, int dtype, unsigned long long sta
   return cudaGetLastError();
 }
 
+// Self-check of the bounded device wait: one thread initializes an mbarrier that expects one
+// arrival, which nothing makes, and waits for its first phase with the tensor-core pass's
+// wait, at most `polls` times. Status 2: the wait gave up, as it must; 1: the phase completed.
+static __device__ unsigned int g_wait_status;
+
+__global__ void k_wait_check(long long polls) {
+  __shared__ unsigned long long mbar;
+  if (threadIdx.x == 0) {
+    tc_mbar_init(&mbar);
+    g_wait_status = tc_wait_bounded(&mbar, 0u, polls) ? 1u : 2u;
+  }
+}
+
 }  // namespace sv
+
+int sv_check_bounded_wait(long long polls, void* stream, int* timed_out) {
+  if (!timed_out || polls < 1 || polls > sv::kTcWaitLimit) return SV_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const unsigned int zero = 0;
+  cudaError_t e = cudaMemcpyToSymbolAsync(sv::g_wait_status, &zero, sizeof(zero), 0, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) {
+    sv::k_wait_check<<<1, 32, 0, st>>>(polls);
+    e = cudaGetLastError();
+  }
+  unsigned int status = 0;
+  if (e == cudaSuccess)
+    e = cudaMemcpyFromSymbolAsync(&status, sv::g_wait_status, sizeof(status), 0, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return SV_ERR_CUDA;
+  if (status != 1u && status != 2u) return SV_ERR_INTERNAL;
+  *timed_out = status == 2u;
+  return SV_OK;
+}

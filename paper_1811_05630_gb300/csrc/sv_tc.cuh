@@ -62,11 +62,11 @@ __device__ __forceinline__ void tc_mbar_init(unsigned long long* mbar) {
   asm volatile("fence.mbarrier_init.release.cluster;");
 }
 
-// Wait for phase `parity` of the mbarrier to complete, polling at most kTcWaitLimit times.
+// Wait for phase `parity` of the mbarrier to complete, polling at most `limit` times.
 // Returns false when the limit ran out.
-__device__ __forceinline__ bool tc_wait(unsigned long long* mbar, uint32_t parity) {
+__device__ __forceinline__ bool tc_wait_bounded(unsigned long long* mbar, uint32_t parity, long long limit) {
   const uint32_t a = tc_smem_u32(mbar);
-  for (long long it = 0; it < kTcWaitLimit; ++it) {
+  for (long long it = 0; it < limit; ++it) {
     uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -76,6 +76,11 @@ __device__ __forceinline__ bool tc_wait(unsigned long long* mbar, uint32_t parit
     if (done) return true;
   }
   return false;
+}
+
+// The tensor-core pass's wait: at most kTcWaitLimit polls.
+__device__ __forceinline__ bool tc_wait(unsigned long long* mbar, uint32_t parity) {
+  return tc_wait_bounded(mbar, parity, kTcWaitLimit);
 }
 
 // Generic-proxy writes of operand tiles become visible to the tensor cores' (async) proxy.

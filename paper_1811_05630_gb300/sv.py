@@ -95,6 +95,7 @@ _SIGS = {
     "sv_batch_apply": ([_vp, _vp, _vp, _i], _i),
     "sv_set_pass_timing": ([_vp, _i], _i),
     "sv_get_pass_timing": ([_vp, _P(_d), _P(_u64), _P(_u64)], _i),
+    "sv_check_bounded_wait": ([ctypes.c_longlong, _vp, _P(_i)], _i),
     "sv_version": ([], ctypes.c_char_p),
 }
 _OPTIONAL = {"sv_set_tensor_cores", "sv_set_spill_pool"}  # absent from builds that predate them
@@ -368,6 +369,14 @@ def codec_decompress(data: torch.Tensor, offsets: torch.Tensor, lengths: torch.T
                                   dtype, float(error_bound), vals.data_ptr(), scratch.data_ptr(),
                                   _stream_handle(stream)), "sv_codec_decompress")
     return vals
+
+
+def check_bounded_wait(polls: int = 1000, stream=None) -> bool:
+    """Run the tensor-core pass's bounded mbarrier wait on a barrier nothing arrives on;
+    True when the wait gave up after `polls` polls (the expected result)."""
+    out = ctypes.c_int(-1)
+    _check(_L.sv_check_bounded_wait(int(polls), _stream_handle(stream), ctypes.byref(out)), "sv_check_bounded_wait")
+    return out.value == 1
 
 
 def version() -> str:
