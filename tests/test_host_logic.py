@@ -59,9 +59,11 @@ class FakeBackend:
                 self.applied = 0
                 self.closed = False
                 self.threads = 0
-                # the fake state holds what admission reserved for a request of its class
+                # the fake state holds metadata and two arenas sized for its peak (1 byte per
+                # amplitude, what stats() reports): at most what admission reserves, before
+                # (prior) and after (learned, with its margin) a request of the class finished
                 req = types.SimpleNamespace(n=n, dtype=dtype, eb=eb)
-                fp = serve.footprint(req, block_log2)
+                fp = serve.footprint(req, block_log2, 1.0)
                 backend.live[id(self)] = fp
                 backend.peak = max(backend.peak, sum(backend.live.values()))
                 backend.created.append(self)
