@@ -39,3 +39,20 @@ def test_product_does_not_use_the_oracle():
                 src = open(os.path.join(dirpath, f)).read()
                 for bad in ("import oracle", "from oracle", "liboracle", "sv_oracle", "orc_"):
                     assert bad not in src, (f, bad)
+
+
+def test_core_calls_cite_the_paper():
+    """Each call of the surveyed boundary is documented with the passage that defines it: the
+    comment block before its declaration, or that block's `name:` entry where one block
+    documents several calls."""
+    txt = open(os.path.join(ROOT, "include", "sv.h")).read()
+    for name in ["sv_create", "sv_apply_gate", "sv_measure_probs", "sv_fidelity", "sv_compressed_bytes"]:
+        decl = re.search(r"^\s*(?:[a-z_0-9]+\s*\**\s+)+%s\s*\(" % name, txt, flags=re.M)
+        assert decl, name
+        start = txt.rfind("/*", 0, decl.start())
+        end = txt.find("*/", start)
+        assert 0 <= start < end < decl.start(), name
+        doc = txt[start:end]
+        entry = re.search(r"\b%s:(.*?)(?=\n \* sv_[a-z_0-9]+:|$)" % name, doc, flags=re.S)
+        text = entry.group(1) if entry else doc
+        assert re.search(r"Sec\. [IVX]+|Algorithm 1", text), (name, text[:200])
