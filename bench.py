@@ -531,8 +531,10 @@ def run_ours(args, rank, world, dist):
                 "alg_bytes_per_launch": alg_bytes / max(npass, 1), "launches": npass,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy bandwidth)"
                 if "fallback" not in pk else "fallback 6.8 TB/s"}
+        # the oracle on the host cores: at N = 1 only (under torchrun the host's cores serve
+        # every rank's replica)
         cpu = (cpu_oracle_sample(wl, args.steps, args.warmup, budget_s=args.cpu_budget)
-               if args.cpu_budget > 0 else None)
+               if args.cpu_budget > 0 and world == 1 else None)
         log("cpu baseline: %s" % (cpu and cpu["value"]))
         # plain GPU path on the same gates, where its vector fits: its time does not depend on
         # the amplitudes' values, so it runs from the basis state
