@@ -10,7 +10,9 @@ Compression" (PMES 2018).
   * ``PlainSim``       — O1, the "original simulator": full amplitude-vector update (Sec. I).
   * ``compress_block`` / ``decompress_block`` — the SZ-style block codec (Sec. II).
   * ``CompressedSim``  — O2, Algorithm 1 (Decompress, Normalize, GateComputation,
-    Compress for every slice, gate by gate).
+    Compress for every slice, gate by gate); with ``lazy=True`` the second mode O2L: slices
+    a gate leaves unchanged keep their streams and hold their pending normalization as a
+    per-slice scale (see sv_oracle.h).
   * ``huffman_lengths`` — the two-queue Huffman code lengths the codec uses.
 
 Parity pins (tests/test_oracle_*.py) check every function here against closed forms,
@@ -106,6 +108,12 @@ def _load():
         L.orc_csim_total_bytes.argtypes = [vp]
         L.orc_csim_total_bytes.restype = u64
         L.orc_csim_load.argtypes = [vp, vp]
+        L.orc_csim_set_lazy.argtypes = [vp, i]
+        L.orc_csim_set_lazy.restype = i
+        L.orc_csim_scales.argtypes = [vp, vp]
+        L.orc_csim_skipped.argtypes = [vp]
+        L.orc_csim_skipped.restype = u64
+        L.orc_csim_read_values.argtypes = [vp, vp]
         _lib = L
         return L
 
@@ -187,16 +195,19 @@ class PlainSim:
 
 
 class CompressedSim:
-    """O2: Algorithm 1 over a block-compressed state (see sv_oracle.c)."""
+    """O2: Algorithm 1 over a block-compressed state (see sv_oracle.c); ``lazy``: the second
+    mode O2L (lazy normalization with slice skipping, see sv_oracle.h)."""
 
     def __init__(self, n: int, slice_log2: int, block_log2: int, dtype: int, eb: float, basis_index: int = 0,
-                 chunk: int = 32):
+                 chunk: int = 32, lazy: bool = False):
         self.n, self.slice_log2, self.block_log2, self.dtype, self.eb = n, slice_log2, block_log2, dtype, eb
         self.chunk = chunk
         self._L = _load()
         self._h = self._L.orc_csim_create_k(n, slice_log2, block_log2, dtype, eb, basis_index, chunk)
         if not self._h:
             raise ValueError("orc_csim_create rejected its arguments")
+        if lazy and self._L.orc_csim_set_lazy(self._h, 1) != 0:
+            raise ValueError("orc_csim_set_lazy refused")
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -240,3 +251,19 @@ class CompressedSim:
 
     def total_bytes(self) -> int:
         return int(self._L.orc_csim_total_bytes(self._h))
+
+    def scales(self) -> np.ndarray:
+        """Pending normalization c_s per slice (all 1 outside the second mode)."""
+        out = np.zeros(1 << (self.n - self.slice_log2), dtype=np.float64)
+        self._L.orc_csim_scales(self._h, _ptr(out))
+        return out
+
+    @property
+    def skipped(self) -> int:
+        return int(self._L.orc_csim_skipped(self._h))
+
+    def read_values(self) -> np.ndarray:
+        """The represented amplitudes c_s x' (complex128 for either dtype)."""
+        out = np.zeros(1 << self.n, dtype=np.complex128)
+        self._L.orc_csim_read_values(self._h, _ptr(out))
+        return out

@@ -9,7 +9,8 @@
  *   Sec. II   — SZ error-bounded lossy compression of state-vector slices, error bound set
  *               by the user (the codec below, restated: quantization, Lorenzo, Huffman).
  *   Alg. 1    — for each gate, for each slice: Decompress, Normalize, GateComputation,
- *               Compress (O2 below).
+ *               Compress (O2 below); O2L, its second mode, skips the slices a gate leaves
+ *               unchanged and keeps their normalization as a per-slice scale.
  * Where the paper is silent (error-bound mode, what "Normalize" scales by, the codec's
  * internals, gates whose targets span slices) this file follows the readings recorded in
  * the design notes; each such place says which reading it takes.
@@ -701,6 +702,12 @@ struct orc_csim {
   size_t* lens;
   orc_block_info* infos;
   double norm;
+  /* the second mode (lazy normalization with slice skipping): a slice the gate leaves
+   * unchanged keeps its stream, and its pending normalization is a scale c_s; the state
+   * it represents is c_s x' (x' the stored values). Outside the mode every c_s is 1. */
+  int lazy;
+  double* scale;     /* one per slice */
+  uint64_t skipped;  /* slices left unchanged by the passes so far */
 };
 
 /* Norm of the stored state (Alg. 1 Normalize; reading: one global scale per gate pass,
@@ -709,15 +716,18 @@ struct orc_csim {
  *   Sd = fl( fl((double)S_hi * 2^64) + (double)S_lo ),  S = exact sum of q^2
  *   V  = pairwise sum over blocks (level by level, a[i] = a[2i] + a[2i+1]) of the
  *        per-block verbatim sums.                                                     */
-static double stored_norm(const orc_csim* s) {
+/* The same formula over blocks [b0, b1) (a power-of-two count) whose slices are selected by
+ * `keep` (NULL: all): S and V sum only the kept blocks (the others count as 0 in V's tree). */
+static double norm_of_blocks(const orc_csim* s, uint64_t b0, uint64_t b1, const unsigned char* keep) {
+  const uint64_t per_slice = (uint64_t)1 << (s->slice_log2 - s->block_log2);
   u128 S = 0;
-  for (uint64_t b = 0; b < s->nblocks; ++b)
-    S += ((u128)s->infos[b].sq_hi << 64) | (u128)s->infos[b].sq_lo;
+  for (uint64_t b = b0; b < b1; ++b)
+    if (!keep || keep[b / per_slice]) S += ((u128)s->infos[b].sq_hi << 64) | (u128)s->infos[b].sq_lo;
   uint64_t hi = (uint64_t)(S >> 64), lo = (uint64_t)S;
   double Sd = (double)hi * 18446744073709551616.0 + (double)lo;
-  double* a = (double*)malloc(sizeof(double) * s->nblocks);
-  for (uint64_t b = 0; b < s->nblocks; ++b) a[b] = s->infos[b].vsum;
-  uint64_t cnt = s->nblocks;
+  uint64_t cnt = b1 - b0;
+  double* a = (double*)malloc(sizeof(double) * cnt);
+  for (uint64_t b = b0; b < b1; ++b) a[b - b0] = (!keep || keep[b / per_slice]) ? s->infos[b].vsum : 0.0;
   while (cnt > 1) {
     for (uint64_t i = 0; i < cnt / 2; ++i) a[i] = a[2 * i] + a[2 * i + 1];
     cnt /= 2;
@@ -727,6 +737,36 @@ static double stored_norm(const orc_csim* s) {
   double two2 = s->qp.two * s->qp.two;
   double t = Sd * two2;
   return t + V;
+}
+
+/* Second mode: N = fl(N_1 + R), N_1 the formula above over the slices whose scale is exactly
+ * 1, R the pairwise sum over slices (level by level, 0 for slices of scale 1) of
+ * fl(fl(c_s c_s) N_s), N_s the formula over slice s's own blocks. With every scale 1 this is
+ * the formula above exactly. */
+static double stored_norm(const orc_csim* s) {
+  if (!s->lazy) return norm_of_blocks(s, 0, s->nblocks, NULL);
+  const uint64_t ns = (uint64_t)1 << (s->n - s->slice_log2);
+  const uint64_t per_slice = (uint64_t)1 << (s->slice_log2 - s->block_log2);
+  unsigned char* one = (unsigned char*)malloc(ns);
+  double* r = (double*)malloc(sizeof(double) * ns);
+  for (uint64_t i = 0; i < ns; ++i) {
+    one[i] = s->scale[i] == 1.0;
+    r[i] = 0.0;
+    if (!one[i]) {
+      const double Ns = norm_of_blocks(s, i * per_slice, (i + 1) * per_slice, NULL);
+      r[i] = (s->scale[i] * s->scale[i]) * Ns;
+    }
+  }
+  const double N1 = norm_of_blocks(s, 0, s->nblocks, one);
+  uint64_t cnt = ns;
+  while (cnt > 1) {
+    for (uint64_t i = 0; i < cnt / 2; ++i) r[i] = r[2 * i] + r[2 * i + 1];
+    cnt /= 2;
+  }
+  const double R = r[0];
+  free(one);
+  free(r);
+  return N1 + R;
 }
 
 static void set_block(orc_csim* s, uint64_t b, const void* vals) {
@@ -764,6 +804,8 @@ orc_csim* orc_csim_create_k(int n, int slice_log2, int block_log2, int dtype, do
   s->streams = (uint8_t**)calloc(s->nblocks, sizeof(uint8_t*));
   s->lens = (size_t*)calloc(s->nblocks, sizeof(size_t));
   s->infos = (orc_block_info*)calloc(s->nblocks, sizeof(orc_block_info));
+  s->scale = (double*)malloc(sizeof(double) * ((size_t)1 << (n - slice_log2)));
+  for (uint64_t i = 0; i < ((uint64_t)1 << (n - slice_log2)); ++i) s->scale[i] = 1.0;
   size_t B = (size_t)1 << block_log2;
   size_t cs = (size_t)comp_size(dtype);
   void* vals = calloc(2 * B, cs);
@@ -784,7 +826,35 @@ void orc_csim_destroy(orc_csim* s) {
   free(s->streams);
   free(s->lens);
   free(s->infos);
+  free(s->scale);
   free(s);
+}
+
+int orc_csim_set_lazy(orc_csim* s, int on) {
+  const uint64_t ns = (uint64_t)1 << (s->n - s->slice_log2);
+  for (uint64_t i = 0; i < ns; ++i)
+    if (s->scale[i] != 1.0) return -1; /* a pending scale belongs to the mode */
+  s->lazy = on != 0;
+  return 0;
+}
+void orc_csim_scales(const orc_csim* s, double* out) {
+  const uint64_t ns = (uint64_t)1 << (s->n - s->slice_log2);
+  for (uint64_t i = 0; i < ns; ++i) out[i] = s->scale[i];
+}
+uint64_t orc_csim_skipped(const orc_csim* s) { return s->skipped; }
+
+/* The represented amplitudes c_s x' as FP64 (re, im) pairs, for either dtype. */
+void orc_csim_read_values(const orc_csim* s, double* out) {
+  const size_t B = (size_t)1 << s->block_log2;
+  const size_t cs = (size_t)comp_size(s->dtype);
+  const uint64_t per_slice = (uint64_t)1 << (s->slice_log2 - s->block_log2);
+  uint8_t* tmp = (uint8_t*)malloc(2 * B * cs);
+  for (uint64_t b = 0; b < s->nblocks; ++b) {
+    orc_decompress_block_k(s->streams[b], s->lens[b], s->block_log2, s->dtype, s->eb, s->chunk, tmp);
+    const double c = s->scale[b / per_slice];
+    for (size_t j = 0; j < 2 * B; ++j) out[b * 2 * B + j] = c * load_val(tmp, s->dtype, j);
+  }
+  free(tmp);
 }
 
 double orc_csim_norm(const orc_csim* s) { return s->norm; }
@@ -812,6 +882,7 @@ void orc_csim_load(orc_csim* s, const void* values) {
   size_t cs = (size_t)comp_size(s->dtype);
   for (uint64_t b = 0; b < s->nblocks; ++b)
     set_block(s, b, (const uint8_t*)values + b * 2 * B * cs);
+  for (uint64_t i = 0; i < ((uint64_t)1 << (s->n - s->slice_log2)); ++i) s->scale[i] = 1.0;
   s->norm = stored_norm(s);
 }
 
@@ -846,6 +917,27 @@ int orc_csim_apply(orc_csim* s, const double* G, const int* targets, int k, cons
   size_t* new_lens = (size_t*)calloc(s->nblocks, sizeof(size_t));
   size_t bound = orc_block_bound(bl, s->dtype);
   uint8_t* tmp = (uint8_t*)malloc(bound);
+  /* second mode: slot g of a group is left unchanged when the group's controls above the
+   * slice are not all 1, or when G is diagonal with every entry of the slot's rows (the rows
+   * whose high-target bits are g) exactly 1 */
+  const uint64_t chigh = cmask >> sl;  /* controls above the slice, as slice-index bits */
+  int unit_slot[32];
+  {
+    int diag = 1;
+    for (int j = 0; j < K; ++j)
+      for (int m = 0; m < K; ++m)
+        if (j != m && (G[2 * (j * K + m)] != 0.0 || G[2 * (j * K + m) + 1] != 0.0)) diag = 0;
+    int tl[5];
+    for (int lh = 0; lh < h; ++lh)
+      for (int l = 0; l < k; ++l)
+        if (targets[l] == high[lh]) tl[lh] = l;
+    for (int g = 0; g < G_; ++g) unit_slot[g] = diag;
+    for (int j = 0; j < K; ++j) {
+      int g = 0;
+      for (int lh = 0; lh < h; ++lh) g |= ((j >> tl[lh]) & 1) << lh;
+      if (!(G[2 * (j * K + j)] == 1.0 && G[2 * (j * K + j) + 1] == 0.0)) unit_slot[g] = 0;
+    }
+  }
 
   for (uint64_t base_slice = 0; base_slice < nslices; ++base_slice) {
     if (base_slice & hmask) continue;
@@ -855,6 +947,26 @@ int orc_csim_apply(orc_csim* s, const double* G, const int* targets, int k, cons
         if ((g >> l) & 1) sid |= (uint64_t)1 << (high[l] - sl);
       slice_ids[g] = sid;
     }
+    int untouched[32], any_touched = 0;
+    for (int g = 0; g < G_; ++g) {
+      untouched[g] = s->lazy && ((base_slice & chigh) != chigh || unit_slot[g]);
+      if (!untouched[g]) any_touched = 1;
+    }
+    if (!any_touched) {
+      /* the group keeps its streams; each slice's pending scale takes this pass's sigma */
+      for (int g = 0; g < G_; ++g) {
+        for (size_t bi = 0; bi < S / B; ++bi) {
+          uint64_t blk = (slice_ids[g] << (sl - bl)) + bi;
+          new_streams[blk] = s->streams[blk];
+          new_lens[blk] = s->lens[blk];
+          new_infos[blk] = s->infos[blk];
+          s->streams[blk] = NULL;
+        }
+        s->scale[slice_ids[g]] = s->scale[slice_ids[g]] * sigma;
+        s->skipped++;
+      }
+      continue;
+    }
     /* Decompress(S) for every slice of the group */
     for (int g = 0; g < G_; ++g)
       for (size_t bi = 0; bi < S / B; ++bi) {
@@ -862,10 +974,17 @@ int orc_csim_apply(orc_csim* s, const double* G, const int* targets, int k, cons
         orc_decompress_block_k(s->streams[blk], s->lens[blk], bl, s->dtype, s->eb, s->chunk,
                                buf + ((size_t)g * S + bi * B) * 2 * cs);
       }
-    /* Normalize(S) */
-    for (size_t e = 0; e < (size_t)G_ * S * 2; ++e) {
-      if (s->dtype == ORC_C128) ((double*)buf)[e] = sigma * ((double*)buf)[e];
-      else ((float*)buf)[e] = sigma_f * ((float*)buf)[e];
+    /* Normalize(S); second mode: the slice's pending scale joins sigma, t = fl(sigma c_s),
+     * and a slice left unchanged is not scaled (only a diagonal gate leaves some slots of a
+     * processed group unchanged, and those slots' values then pass the gate unmixed) */
+    for (int g = 0; g < G_; ++g) {
+      if (untouched[g]) continue;
+      const double t = s->lazy ? sigma * s->scale[slice_ids[g]] : sigma;
+      const float t_f = s->lazy ? (float)t : sigma_f;
+      for (size_t e = (size_t)g * S * 2; e < (size_t)(g + 1) * S * 2; ++e) {
+        if (s->dtype == ORC_C128) ((double*)buf)[e] = t * ((double*)buf)[e];
+        else ((float*)buf)[e] = t_f * ((float*)buf)[e];
+      }
     }
     /* GateComputation(G, S): global index i lives in group slot g (its high-target bits)
      * at offset i mod S */
@@ -913,7 +1032,19 @@ int orc_csim_apply(orc_csim* s, const double* G, const int* targets, int k, cons
       }
     }
     /* Compress(S) */
-    for (int g = 0; g < G_; ++g)
+    for (int g = 0; g < G_; ++g) {
+      if (untouched[g]) {  /* second mode: the stream stays, the scale takes sigma */
+        for (size_t bi = 0; bi < S / B; ++bi) {
+          uint64_t blk = (slice_ids[g] << (sl - bl)) + bi;
+          new_streams[blk] = s->streams[blk];
+          new_lens[blk] = s->lens[blk];
+          new_infos[blk] = s->infos[blk];
+          s->streams[blk] = NULL;
+        }
+        s->scale[slice_ids[g]] = s->scale[slice_ids[g]] * sigma;
+        s->skipped++;
+        continue;
+      }
       for (size_t bi = 0; bi < S / B; ++bi) {
         uint64_t blk = (slice_ids[g] << (sl - bl)) + bi;
         size_t len = orc_compress_block_k(buf + ((size_t)g * S + bi * B) * 2 * cs, bl, s->dtype,
@@ -922,6 +1053,8 @@ int orc_csim_apply(orc_csim* s, const double* G, const int* targets, int k, cons
         memcpy(new_streams[blk], tmp, len);
         new_lens[blk] = len;
       }
+      s->scale[slice_ids[g]] = 1.0;
+    }
   }
   for (uint64_t b = 0; b < s->nblocks; ++b) free(s->streams[b]);
   free(s->streams);

@@ -98,6 +98,24 @@ uint64_t orc_csim_total_bytes(const orc_csim* s);
 /* Replace the stored state by the compression of `values` (2^n amplitudes). */
 void orc_csim_load(orc_csim* s, const void* values);
 
+/* ---- O2L: the second mode, lazy normalization with slice skipping ----
+ * Algorithm 1 visits every slice with every gate. In this mode a slice the gate leaves
+ * unchanged (the group's controls above the slice are not all 1, or G is diagonal with every
+ * entry of the slice's rows exactly 1) is not decompressed or recompressed: its stream stays
+ * and its pending normalization is kept as a scale c_s (c_s <- fl(c_s sigma)); the state it
+ * represents is c_s x'. A slice the gate changes is normalized with t = fl(sigma c_s) in
+ * place of sigma and recompressed with c_s = 1. The stored norm becomes fl(N_1 + R): N_1 the
+ * O2 formula over the slices of scale 1, R the pairwise sum over slices of fl(fl(c_s c_s) N_s).
+ * With every scale 1 and no slice skipped a pass is O2's pass exactly. Results differ from
+ * O2 otherwise (skipped slices are not requantized).
+ * set_lazy: switch the mode (-1 while a scale is pending). scales: c_s per slice (2^(n -
+ * slice_log2) doubles). skipped: slices left unchanged so far. read_values: c_s x' as FP64
+ * (re, im) pairs for either dtype. */
+int orc_csim_set_lazy(orc_csim* s, int on);
+void orc_csim_scales(const orc_csim* s, double* out);
+uint64_t orc_csim_skipped(const orc_csim* s);
+void orc_csim_read_values(const orc_csim* s, double* out);
+
 #ifdef __cplusplus
 }
 #endif
